@@ -1,0 +1,338 @@
+"""Exact local estimator of Phase 1 (Algorithm 1, Sec. III-B), oracle only.
+
+Reading of the paper: LocalDecoder(H_v, s_v) returns the exact bitwise posterior under the
+channel prior,
+
+    q_{v,j} = P(e_j = 1 | H_v e = s_v) = sum_{e: H_v e = s_v} e_j pi(e) / sum_{e: H_v e = s_v} pi(e),
+
+and the hard decision e_v = the coset member of least weight (the maximum-likelihood member
+under a uniform prior p < 1/2), ties broken by the least row-major key
+K(e) = sum_{a,b} E[a][b] 2^(a*Delta + b). The paper uses BP-LSD here and does not say which
+soft vector it passes on; exact marginals are what LSD/OSD approximate.
+
+With a uniform prior p, pi(e) = (1-p)^(n_l) r^wt(e) with r = p/(1-p), so
+
+    q_{v,j} = N1_s,j(r) / N_s(r),   N_s(t) = sum_w N_s[w] t^w,  N1_s,j(t) = sum_w N1_s[j][w] t^w,
+
+where N_s[w] counts the coset members of weight w and N1_s[j][w] those of them with e_j = 1.
+These integer tables depend only on the local code, not on p.
+
+How the tables are computed. Two exact integer identities for the defining sums are
+implemented and must agree entry for entry:
+
+* Fourier form (``fourier_tables``, the one ``tables`` uses): the indicator of H_v e = s is
+  2^-m_l sum_u (-1)^(u.(H_v e + s)), and the weight-w sum of (-1)^(c.e) over e is the
+  Krawtchouk value K_w(wt c), so N_s[w] = 2^-m_l sum_u (-1)^(u.s) K_w(wt(u H_v)).
+* Row grouping (``row_tables``): the local check matrix is L = kron(R_B, R_A) (local index
+  j = b*Delta + a), so for the Delta x Delta view E, L vec(E) = vec(R_A E R_B^T); writing
+  f_a = R_B x_a for row a of E, the syndrome is S = R_A F with F the matrix of rows f_a, and
+  the sum over E is a sum over the row images F with R_A F = S of the product over rows of
+  P(f_a)(t) = sum_{x: R_B x = f_a} t^wt(x).
+
+Further pins: brute force over all 2^(Delta^2) patterns for Delta = 4, the closed-form
+marginals sum_s N_s[w] = C(n_l, w) and coset sizes 2^(n_l - m_l), MacWilliams on the zero
+coset, and brute force over the coset for sampled syndromes at Delta = 6.
+"""
+from __future__ import annotations
+
+import functools
+from math import comb
+
+import numpy as np
+
+
+def _poly_mul(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Row-wise product of integer polynomials: (N, da) x (N, db) -> (N, da+db-1)."""
+    N, da = a.shape
+    db = b.shape[1]
+    out = np.zeros((N, da + db - 1), dtype=np.int64)
+    for d in range(db):
+        out[:, d:d + da] += a * b[:, d:d + 1]
+    return out
+
+
+def _row_tables(RB: np.ndarray):
+    """For every row pattern x in F_2^Delta (bit b = x_b): f = R_B x as an integer (bit rB),
+    its weight, and the per-(f) polynomials P(f)[w] and P_b(f)[w]."""
+    kB, delta = RB.shape
+    xs = np.arange(1 << delta)
+    bits = (xs[:, None] >> np.arange(delta)[None, :]) & 1          # (2^Delta, Delta)
+    f = ((bits @ RB.T.astype(np.int64)) & 1) @ (1 << np.arange(kB))
+    wt = bits.sum(axis=1)
+    P = np.zeros((1 << kB, delta + 1), dtype=np.int64)
+    Pb = np.zeros((delta, 1 << kB, delta + 1), dtype=np.int64)
+    for x in range(1 << delta):
+        P[f[x], wt[x]] += 1
+        for b in range(delta):
+            if bits[x, b]:
+                Pb[b, f[x], wt[x]] += 1
+    return f, wt, bits, P, Pb
+
+
+@functools.lru_cache(maxsize=16)
+def _tables_cached(ra_bytes, ra_shape, rb_bytes, rb_shape):
+    RA = np.frombuffer(ra_bytes, dtype=np.uint8).reshape(ra_shape)
+    RB = np.frombuffer(rb_bytes, dtype=np.uint8).reshape(rb_shape)
+    N, N1 = fourier_tables(np.kron(RB, RA).astype(np.uint8))
+    return N, N1, ml_decisions(RA, RB)
+
+
+def tables(RA: np.ndarray, RB: np.ndarray):
+    """(N, N1, ml_mask): N (2^m_l, n_l+1), N1 (2^m_l, n_l, n_l+1) int64, ml_mask (2^m_l,) int64
+    bit j = local index j of the ML hard decision. Cached per local code."""
+    RA = np.ascontiguousarray(RA, dtype=np.uint8)
+    RB = np.ascontiguousarray(RB, dtype=np.uint8)
+    return _tables_cached(RA.tobytes(), RA.shape, RB.tobytes(), RB.shape)
+
+
+def _row_images(RA: np.ndarray, RB: np.ndarray):
+    """All row-image matrices F (f_a = (F >> a*kB) & mask) and their syndromes S = R_A F."""
+    kA, delta = RA.shape
+    kB = RB.shape[0]
+    NF = 1 << (delta * kB)
+    Fidx = np.arange(NF, dtype=np.int64)
+    fa = np.stack([(Fidx >> (a * kB)) & ((1 << kB) - 1) for a in range(delta)])   # (Delta, NF)
+    s_of_F = np.zeros(NF, dtype=np.int64)
+    for rA in range(kA):
+        for rB in range(kB):
+            bit = np.zeros(NF, dtype=np.int64)
+            for a in range(delta):
+                if RA[rA, a]:
+                    bit ^= (fa[a] >> rB) & 1
+            s_of_F |= bit << (rB * kA + rA)
+    return fa, s_of_F
+
+
+def ml_decisions(RA: np.ndarray, RB: np.ndarray) -> np.ndarray:
+    """ML hard decision per syndrome (least weight, then least row-major key), by grouping the
+    coset by row images: for fixed F the members are products of independent row choices, so
+    the best member takes in every row the least-weight, least-valued pattern x with R_B x = f_a;
+    the best F minimises (total weight, key)."""
+    kA, delta = RA.shape
+    kB = RB.shape[0]
+    m_l = kA * kB
+    f_of_x, wt_of_x, _, _, _ = _row_tables(RB)
+    fa, s_of_F = _row_images(RA, RB)
+    minwt = np.full(1 << kB, 10 ** 9, dtype=np.int64)
+    xmin = np.zeros(1 << kB, dtype=np.int64)
+    for x in range(1 << delta):          # increasing x: first hit of the least weight is least x
+        f = f_of_x[x]
+        if wt_of_x[x] < minwt[f]:
+            minwt[f] = wt_of_x[x]
+            xmin[f] = x
+    cost = sum(minwt[fa[a]] for a in range(delta))
+    key = sum(xmin[fa[a]] << (a * delta) for a in range(delta))
+    best_key = np.full(1 << m_l, -1, dtype=np.int64)
+    srt = np.lexsort((key, cost))         # increasing (cost, key)
+    s_sorted = s_of_F[srt]
+    first = np.unique(s_sorted, return_index=True)[1]
+    best_key[s_sorted[first]] = key[srt][first]
+    ml_mask = np.zeros(1 << m_l, dtype=np.int64)
+    for a in range(delta):
+        for b in range(delta):
+            bit = (best_key >> (a * delta + b)) & 1
+            ml_mask |= bit << (b * delta + a)
+    return ml_mask
+
+
+def row_tables(RA: np.ndarray, RB: np.ndarray):
+    """(N, N1) by grouping the defining sums by row images (see module doc)."""
+    kA, delta = RA.shape
+    kB = RB.shape[0]
+    m_l = kA * kB
+    n_l = delta * delta
+    f_of_x, wt_of_x, _, P, Pb = _row_tables(RB)
+    NF = 1 << (delta * kB)
+    fa, s_of_F = _row_images(RA, RB)
+    order = np.argsort(s_of_F, kind="stable")
+    per = NF >> m_l
+    if not (np.bincount(s_of_F, minlength=1 << m_l) == per).all():
+        raise ValueError("local check matrix is not full rank")
+
+    def group_sum(T):
+        return T[order].reshape(1 << m_l, per, T.shape[1]).sum(axis=1)
+
+    prod = P[fa[0]]
+    for a in range(1, delta):
+        prod = _poly_mul(prod, P[fa[a]])
+    N = group_sum(prod)
+
+    N1 = np.zeros((1 << m_l, n_l, n_l + 1), dtype=np.int64)
+    # product over the other rows a2 != a, as (rows before a) * (rows after a)
+    before = [np.ones((NF, 1), dtype=np.int64)]
+    for a in range(delta - 1):
+        before.append(_poly_mul(before[-1], P[fa[a]]))
+    after = [np.ones((NF, 1), dtype=np.int64)]
+    for a in range(delta - 1, 0, -1):
+        after.append(_poly_mul(after[-1], P[fa[a]]))
+    after = after[::-1]                    # after[a] = product over rows > a
+    for a in range(delta):
+        Q = _poly_mul(before[a], after[a])
+        for b in range(delta):
+            T = _poly_mul(Q, Pb[b][fa[a]])
+            N1[:, b * delta + a, :] = group_sum(T)
+
+    return N, N1
+
+
+def posterior_from_tables(N: np.ndarray, N1: np.ndarray, p: float) -> np.ndarray:
+    """q[s, j] in FP64: ratio of the two enumerator polynomials at r = p/(1-p), each evaluated
+    by Horner's rule from the highest degree (separate IEEE multiply and add)."""
+    if not (0.0 < p < 0.5):
+        raise ValueError("the uniform prior must satisfy 0 < p < 1/2")
+    r = p / (1.0 - p)
+    deg = N.shape[-1] - 1
+    num = np.zeros(N1.shape[:2], dtype=np.float64)
+    den = np.zeros(N.shape[0], dtype=np.float64)
+    for w in range(deg, -1, -1):
+        num = num * r + N1[:, :, w].astype(np.float64)
+        den = den * r + N[:, w].astype(np.float64)
+    return num / den[:, None]
+
+
+def brute_force(L: np.ndarray, delta: int):
+    """(N, N1, ml_mask) by enumerating all 2^(Delta^2) local patterns (small Delta only)."""
+    m_l, n_l = L.shape
+    if n_l > 20:
+        raise ValueError("brute force only for tiny local codes")
+    es = np.arange(1 << n_l, dtype=np.int64)
+    bits = ((es[:, None] >> np.arange(n_l)[None, :]) & 1).astype(np.int64)   # bit j = local j
+    s = ((bits @ L.T.astype(np.int64)) & 1) @ (1 << np.arange(m_l))
+    w = bits.sum(axis=1)
+    N = np.zeros((1 << m_l, n_l + 1), dtype=np.int64)
+    np.add.at(N, (s, w), 1)
+    N1 = np.zeros((1 << m_l, n_l, n_l + 1), dtype=np.int64)
+    for j in range(n_l):
+        sel = bits[:, j] == 1
+        np.add.at(N1[:, j, :], (s[sel], w[sel]), 1)
+    # row-major key K(e) = sum E[a][b] 2^(a*Delta+b), local j = b*Delta + a
+    key = np.zeros_like(es)
+    for a in range(delta):
+        for b in range(delta):
+            key |= bits[:, b * delta + a] << (a * delta + b)
+    ml = np.zeros(1 << m_l, dtype=np.int64)
+    best = {}
+    for idx in np.lexsort((key, w)):
+        si = int(s[idx])
+        if si not in best:
+            best[si] = int(es[idx])
+    for si, e in best.items():
+        ml[si] = e
+    return N, N1, ml
+
+
+def posterior_brute_force(L: np.ndarray, s: int, p_vec: np.ndarray) -> np.ndarray:
+    """The defining sum with an arbitrary per-position prior p_vec (small Delta only)."""
+    m_l, n_l = L.shape
+    es = np.arange(1 << n_l, dtype=np.int64)
+    bits = ((es[:, None] >> np.arange(n_l)[None, :]) & 1)
+    syn = ((bits @ L.T.astype(np.int64)) & 1) @ (1 << np.arange(m_l))
+    sel = bits[syn == s].astype(np.float64)
+    pi = np.prod(np.where(sel == 1, p_vec[None, :], 1.0 - p_vec[None, :]), axis=1)
+    return (sel * pi[:, None]).sum(axis=0) / pi.sum()
+
+
+def fourier_tables(L: np.ndarray):
+    """(N, N1) from the Fourier form over the row space of L, in exact integers:
+    N_s[w] = 2^-m_l sum_u (-1)^(u.s) K_w(wt(u L)), K_w(i) = sum_h (-1)^h C(i,h) C(n_l-i, w-h), and
+    N1_s[j][w] = 2^-m_l sum_u (-1)^(u.s) (-1)^(c_j) K'_(w-1)(wt(c) - c_j) with c = u L and K'
+    the Krawtchouk polynomial of length n_l - 1."""
+    m_l, n_l = L.shape
+
+    def kraw(length):
+        K = np.zeros((length + 1, length + 1), dtype=object)   # K[w][i]
+        for w in range(length + 1):
+            for i in range(length + 1):
+                K[w][i] = sum((-1) ** h * comb(i, h) * comb(length - i, w - h)
+                              for h in range(0, min(i, w) + 1) if w - h <= length - i)
+        return np.array(K.tolist(), dtype=np.int64)
+
+    K = kraw(n_l)
+    K1 = kraw(n_l - 1)
+    us = np.arange(1 << m_l, dtype=np.int64)
+    ubits = (us[:, None] >> np.arange(m_l)[None, :]) & 1
+    C = (ubits @ L.astype(np.int64)) & 1                      # (2^m_l, n_l) codewords of rowspace
+    wc = C.sum(axis=1)
+    sgn = 1 - 2 * (np.bitwise_count((us[:, None] & us[None, :]).astype(np.uint64)) & 1).astype(np.int64)
+    # sgn[u, s] = (-1)^(u.s)
+    N = (sgn.T @ K[:, wc].T) >> m_l                            # (2^m_l, n_l+1)
+    N1 = np.zeros((1 << m_l, n_l, n_l + 1), dtype=np.int64)
+    for j in range(n_l):
+        cj = C[:, j]
+        col = np.zeros((1 << m_l, n_l + 1), dtype=np.int64)
+        col[:, 1:] = ((1 - 2 * cj)[:, None] * K1[:, wc - cj].T)
+        N1[:, j, :] = (sgn.T @ col) >> m_l
+    return N, N1
+
+
+def macwilliams_zero_coset(L: np.ndarray) -> np.ndarray:
+    """Weight distribution of ker L from that of its dual (the row space of L) by MacWilliams:
+    W_ker(x, y) = 2^-m_l sum_{c in rowspace L} (x + y)^(n_l - wt c) (x - y)^(wt c)."""
+    m_l, n_l = L.shape
+    us = np.arange(1 << m_l, dtype=np.int64)
+    ubits = (us[:, None] >> np.arange(m_l)[None, :]) & 1
+    wc = (((ubits @ L.astype(np.int64)) & 1).sum(axis=1))
+    out = [0] * (n_l + 1)
+    for i in wc.tolist():
+        # coefficient of x^(n_l-w) y^w in (x+y)^(n_l-i) (x-y)^i
+        for w in range(n_l + 1):
+            out[w] += sum(comb(n_l - i, w - h) * comb(i, h) * (-1) ** h
+                          for h in range(0, min(i, w) + 1) if w - h <= n_l - i)
+    return np.array([x >> m_l for x in out], dtype=np.int64)
+
+
+# ---------------------------------------------------------------------------------------
+# Single-precision decision path. Floating point decides the hard decisions of the global
+# decoder, so the oracle evaluates the prior LLR that feeds it in IEEE binary32 with a fixed
+# operation order: boost and merge in binary32, and the natural logarithm by the inverse
+# hyperbolic tangent series ln m = 2 atanh z, z = (m-1)/(m+1) (Abramowitz & Stegun 4.1.27),
+# on m in [sqrt(1/2), sqrt(2)) after extracting the binary exponent. Coefficients are the
+# nearest binary32 values of 2/k; ln 2 and sqrt 2 likewise.
+# ---------------------------------------------------------------------------------------
+
+def _f32(bits: int) -> np.float32:
+    return np.array([bits], dtype=np.uint32).view(np.float32)[0]
+
+
+LN2_F = _f32(0x3F317218)
+SQRT2_F = _f32(0x3FB504F3)
+SERIES_F = [_f32(0x40000000), _f32(0x3F2AAAAB), _f32(0x3ECCCCCD), _f32(0x3E924925),
+            _f32(0x3E638E39), _f32(0x3E3A2E8C)]          # 2/1, 2/3, 2/5, 2/7, 2/9, 2/11
+P_MIN_F = np.float32(2.0 ** -23)
+P_MAX_F = np.float32(1.0 - 2.0 ** -23)
+
+
+def log_f32(x: np.ndarray) -> np.ndarray:
+    """Natural log of positive normal binary32 values, evaluated in binary32 as described above."""
+    x = np.asarray(x, dtype=np.float32)
+    bits = x.view(np.uint32)
+    e = ((bits >> np.uint32(23)) & np.uint32(0xFF)).astype(np.int32) - 127
+    m = ((bits & np.uint32(0x7FFFFF)) | np.uint32(0x3F800000)).view(np.float32)
+    big = m > SQRT2_F
+    m = np.where(big, m * np.float32(0.5), m).astype(np.float32)
+    e = e + big.astype(np.int32)
+    z = ((m - np.float32(1.0)) / (m + np.float32(1.0))).astype(np.float32)
+    w = (z * z).astype(np.float32)
+    s = np.full(x.shape, SERIES_F[5], dtype=np.float32)
+    for c in (SERIES_F[4], SERIES_F[3], SERIES_F[2], SERIES_F[1], SERIES_F[0]):
+        s = (s * w).astype(np.float32)
+        s = (s + c).astype(np.float32)
+    a = (e.astype(np.float32) * LN2_F).astype(np.float32)
+    b = (z * s).astype(np.float32)
+    return (a + b).astype(np.float32)
+
+
+def llr_f32(p: np.ndarray) -> np.ndarray:
+    """lambda = ln((1 - p)/p) in binary32 after clamping p to [2^-23, 1 - 2^-23]."""
+    p = np.clip(np.asarray(p, dtype=np.float32), P_MIN_F, P_MAX_F).astype(np.float32)
+    x = ((np.float32(1.0) - p) / p).astype(np.float32)
+    return log_f32(x)
+
+
+def boosted_table_f32(N, N1, ml_mask, p: float) -> np.ndarray:
+    """Phase-1 output table in binary32: q rounded to binary32, then max(q, 1/2) on the bits of
+    the ML decision (the boost of Algorithm 1; the ML member always satisfies H_v e = s_v)."""
+    q = posterior_from_tables(N, N1, p).astype(np.float32)
+    n_l = q.shape[1]
+    flip = ((ml_mask[:, None] >> np.arange(n_l)[None, :]) & 1).astype(bool)
+    return np.where(flip, np.maximum(q, np.float32(0.5)), q).astype(np.float32)

@@ -1,0 +1,179 @@
+"""Oracle pins for the exact local estimator (Phase 1 of Algorithm 1)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import local
+
+
+def test_delta4_tables_equal_brute_force(sl3):
+    inst, code = sl3
+    for side in code.sides:
+        N, N1, ml = local.tables(side.RA, side.RB)
+        Nb, N1b, mlb = local.brute_force(side.L, inst.delta)
+        assert (N == Nb).all() and (N1 == N1b).all() and (ml == mlb).all()
+        Nr, N1r = local.row_tables(side.RA, side.RB)
+        assert (N == Nr).all() and (N1 == N1r).all()
+
+
+def test_delta4_posterior_equals_defining_sum(sl3):
+    inst, code = sl3
+    side = code.sides[0]
+    N, N1, _ = local.tables(side.RA, side.RB)
+    for p in (0.02, 0.05, 0.2):
+        q = local.posterior_from_tables(N, N1, p)
+        for s in (0, 1, 5, 11, 15):
+            qb = local.posterior_brute_force(side.L, s, np.full(16, p))
+            assert np.abs(q[s] - qb).max() < 1e-13
+
+
+@pytest.mark.slow
+def test_delta6_fourier_equals_row_grouping(psl7):
+    inst, code = psl7
+    side = code.sides[0]
+    N, N1, _ = local.tables(side.RA, side.RB)
+    Nr, N1r = local.row_tables(side.RA, side.RB)
+    assert (N == Nr).all() and (N1 == N1r).all()
+
+
+@pytest.mark.parametrize("side_id", [0, 1])
+def test_delta6_closed_forms(psl7, side_id):
+    inst, code = psl7
+    side = code.sides[side_id]
+    N, N1, ml = local.tables(side.RA, side.RB)
+    n_l, m_l = 36, side.m_l
+    assert m_l == 9
+    # every coset has 2^(n_l - m_l) members; all cosets together hold C(n_l, w) patterns of weight w
+    assert (N.sum(axis=1) == 2 ** (n_l - m_l)).all()
+    assert [int(x) for x in N.sum(axis=0)] == [math.comb(n_l, w) for w in range(n_l + 1)]
+    # patterns with e_j = 1 of weight w: C(n_l - 1, w - 1) over all cosets, for every j
+    tot = N1.sum(axis=0)
+    for j in range(n_l):
+        assert [int(x) for x in tot[j]] == [0] + [math.comb(n_l - 1, w - 1) for w in range(1, n_l + 1)]
+    # sum_j N1 = w N (each member of weight w has w ones)
+    assert (N1.sum(axis=1) == N * np.arange(n_l + 1)[None, :]).all()
+    # MacWilliams on the zero coset (the local code itself)
+    assert (local.macwilliams_zero_coset(side.L) == N[0]).all()
+    # the ML decision lies in the coset and has the least weight present in it
+    bits = (ml[:, None] >> np.arange(n_l)[None, :]) & 1
+    syn = ((bits @ side.L.T.astype(np.int64)) & 1) @ (1 << np.arange(m_l))
+    assert (syn == np.arange(1 << m_l)).all()
+    assert (bits.sum(axis=1) == np.argmax(N > 0, axis=1)).all()
+
+
+def _coset_brute_force(L, s, delta):
+    """Enumerate the 2^(n_l - m_l) coset members of syndrome s: weight histogram, per-bit
+    histogram of one position, and the least (weight, row-major key) member."""
+    from oracle import gf2
+    m_l, n_l = L.shape
+    ker = gf2.kernel_basis(L)
+    R, piv = gf2.rref(L)
+    # a particular solution: solve L e = s through the RREF of [L | s]
+    aug = np.concatenate([L, np.array([(s >> r) & 1 for r in range(m_l)], dtype=np.uint8)[:, None]], axis=1)
+    Ra, pa = gf2.rref(aug)
+    e0 = np.zeros(n_l, dtype=np.uint8)
+    for i, c in enumerate(pa):
+        e0[c] = Ra[i, -1]
+    # convert local index j = b*Delta + a to row-major key bit a*Delta + b, as 64-bit ints
+    perm = np.array([(j % delta) * delta + (j // delta) for j in range(n_l)])
+
+    def as_key(v):
+        return int(sum(int(v[j]) << int(perm[j]) for j in range(n_l)))
+
+    kvec = np.array([as_key(k) for k in ker], dtype=np.uint64)
+    x0 = np.uint64(as_key(e0))
+    h = kvec.size // 2
+    lo = np.zeros(1, dtype=np.uint64)
+    for k in kvec[:h]:
+        lo = np.concatenate([lo, lo ^ k])
+    hi = np.zeros(1, dtype=np.uint64)
+    for k in kvec[h:]:
+        hi = np.concatenate([hi, hi ^ k])
+    hist = np.zeros(n_l + 1, dtype=np.int64)
+    best = (n_l + 1, None)
+    for c in range(0, lo.size, 256):
+        X = (lo[c:c + 256, None] ^ hi[None, :] ^ x0).ravel()
+        w = np.bitwise_count(X).astype(np.int64)
+        hist += np.bincount(w, minlength=n_l + 1)
+        wm = int(w.min())
+        if wm <= best[0]:
+            cand = int(X[w == wm].min())
+            if wm < best[0] or cand < best[1]:
+                best = (wm, cand)
+    return hist, best
+
+
+@pytest.mark.slow
+def test_delta6_coset_brute_force_sampled(psl7):
+    inst, code = psl7
+    side = code.sides[0]
+    N, N1, ml = local.tables(side.RA, side.RB)
+    delta = inst.delta
+    for s in (0, 77, 300, 511):
+        hist, (wbest, key) = _coset_brute_force(side.L, s, delta)
+        assert (hist == N[s]).all()
+        # ML mask (local order) -> row-major key
+        m = int(ml[s])
+        k2 = sum(((m >> j) & 1) << ((j % delta) * delta + j // delta) for j in range(36))
+        assert wbest == bin(m).count("1") and key == k2
+
+
+def test_posterior_small_p_limit(psl7):
+    """p -> 0: the posterior is uniform over the least-weight coset members."""
+    inst, code = psl7
+    side = code.sides[0]
+    N, N1, _ = local.tables(side.RA, side.RB)
+    q = local.posterior_from_tables(N, N1, 1e-9)
+    wmin = np.argmax(N > 0, axis=1)
+    lim = N1[np.arange(512), :, wmin] / N[np.arange(512), wmin][:, None]
+    assert np.abs(q - lim).max() < 1e-6
+
+
+def test_posterior_fourier_form_fp64(psl7):
+    """Dual-domain closed form of the marginal in FP64 (well conditioned at p = 0.2)."""
+    inst, code = psl7
+    side = code.sides[0]
+    L = side.L.astype(np.int64)
+    N, N1, _ = local.tables(side.RA, side.RB)
+    p = 0.2
+    q = local.posterior_from_tables(N, N1, p)
+    rho = 1 - 2 * p
+    us = np.arange(512)
+    ub = (us[:, None] >> np.arange(9)[None, :]) & 1
+    C = (ub @ L) & 1
+    for s in (3, 100, 400):
+        sg = (-1.0) ** (np.bitwise_count((us & s).astype(np.uint64)).astype(np.int64) & 1)
+        T = (sg * rho ** C.sum(axis=1)).sum()
+        for j in (0, 17, 35):
+            Tj = (sg * rho ** (C.sum(axis=1) + 1 - 2 * C[:, j])).sum()
+            assert abs((1 - Tj / T) / 2 - q[s, j]) < 1e-12
+
+
+def test_log_f32_accuracy():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([np.exp(rng.uniform(-16.5, 16.5, 200000)), [1.0, 2.0, 0.5, 1.4142135, 1.4142137]])
+    x = x.astype(np.float32)
+    got = local.log_f32(x).astype(np.float64)
+    ref = np.log(x.astype(np.float64))
+    assert np.abs(got - ref).max() < 4e-6
+    assert np.abs((got - ref) / np.maximum(np.abs(ref), 1e-3)).max() < 1e-5
+
+
+def test_llr_f32_matches_fp64():
+    p = np.linspace(1e-6, 1 - 1e-6, 100001)
+    got = local.llr_f32(p.astype(np.float32)).astype(np.float64)
+    p32 = p.astype(np.float32).astype(np.float64)
+    ref = np.log((1 - p32) / p32)
+    assert np.abs(got - ref).max() < 1e-5
+
+
+def test_boost_applies_to_ml_bits(psl7):
+    inst, code = psl7
+    side = code.sides[0]
+    N, N1, ml = local.tables(side.RA, side.RB)
+    lut = local.boosted_table_f32(N, N1, ml, 0.05)
+    q = local.posterior_from_tables(N, N1, 0.05).astype(np.float32)
+    flip = ((ml[:, None] >> np.arange(36)[None, :]) & 1).astype(bool)
+    assert (lut[flip] >= 0.5).all()
+    assert (lut[~flip] == q[~flip]).all()
