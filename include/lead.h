@@ -1,0 +1,237 @@
+/*
+ * lead.h -- C ABI of the GB300 (sm_103a) LEAD decoding library.
+ *
+ * LEAD ("A Local Ensemble-Assisted Parallel Decoding Framework for Quantum Tanner Codes")
+ * decodes a quantum Tanner code in three phases (Algorithm 1, Sec. III-B):
+ *   Phase 1  every vertex v of one side of the left-right Cayley complex estimates the error
+ *            probabilities of the Delta^2 qubits of its local view from its local syndrome
+ *            s_v, and boosts the bits of its local hard decision to at least 1/2;
+ *   Phase 2  the two estimates of every qubit are averaged and scaled by alpha (soft-information
+ *            regularisation) into a global prior;
+ *   Phase 3  a global decoder (here flooding min-sum, at most max_iter iterations, with a
+ *            bit-packed check H e = s after every iteration) produces the correction.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: LEAD_OK (0) or a negative LEAD_E* code; no exception crosses the ABI.
+ *    lead_status_string() names a code.
+ *  - Sides: side 0 decodes X errors from the H_Z syndrome (Z-generators on V0, Sec. II-B);
+ *    side 1 decodes Z errors from the H_X syndrome (X-generators on V1).
+ *  - Bit vectors are arrays of uint32 words, one row per shot, bit j of word w = element
+ *    32 w + j. Error and correction rows have lead_code_info.words_n words, syndrome rows
+ *    lead_code_info.words_m[side] words (both rounded up to a multiple of 4 words = 16 bytes);
+ *    padding bits are written as 0 and must be 0 on input.
+ *  - Pointers marked (dev) are device pointers of the device the code was prepared on,
+ *    (host) are host pointers. The caller owns and allocates every buffer it passes; the
+ *    library owns only the code object and its device tables.
+ *  - stream: a cudaStream_t passed as void*; NULL means the legacy default stream. All device
+ *    work of a call is enqueued on that stream and nothing synchronises with the host, except
+ *    where a call says so.
+ *  - Sizes and layouts the library cannot serve return LEAD_EINVAL before any device work.
+ */
+#ifndef LEAD_H
+#define LEAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LEAD_OK         0
+#define LEAD_EINVAL    -1   /* bad argument, size or layout                                    */
+#define LEAD_ENOTTNC   -2   /* A, B violate Total No-Conjugacy: ag == gb for some a, b, g      */
+#define LEAD_ENOTSYM   -3   /* A or B not closed under inversion, repeated, or contains 1      */
+#define LEAD_ECSS      -4   /* construction produced H_X H_Z^T != 0 (internal invariant)       */
+#define LEAD_EOOM      -5   /* host or device allocation failed                                */
+#define LEAD_ECUDA     -6   /* a CUDA runtime call failed                                      */
+#define LEAD_ETIMEOUT  -7   /* a bounded device wait expired                                   */
+#define LEAD_ESTATE    -8   /* code not prepared on a device, or prepared on another device    */
+#define LEAD_ENOTGROUP -9   /* the table is not a group table (identity or inverses missing)   */
+
+/* noise models of lead_sample (Sec. IV-A uses depolarizing noise) */
+#define LEAD_NOISE_X      0  /* i.i.d. X flips with probability p (code capacity)              */
+#define LEAD_NOISE_Z      1  /* i.i.d. Z flips with probability p                               */
+#define LEAD_NOISE_DEPOL  2  /* X, Y, Z each with probability p/3                               */
+
+/* per-shot decode status bits */
+#define LEAD_ST_CONVERGED 1  /* the returned correction satisfies H e = s                     */
+#define LEAD_ST_MAX_ITER  2  /* no iteration up to max_iter satisfied H e = s: decoder failure */
+
+/* precision modes of lead_decode_opts.precision */
+#define LEAD_PREC_FP32    0  /* binary32 priors and messages                                   */
+
+typedef struct lead_code lead_code;   /* opaque; immutable after lead_build_code */
+
+/* A finite group given by its Cayley table: mul[i * order + j] = index of g_i g_j (host). */
+typedef struct {
+  int32_t order;
+  const int32_t* mul;
+} lead_group;
+
+typedef struct {
+  int32_t n;              /* qubits = |G| Delta^2 / 2 (Sec. III-C)                              */
+  int32_t order;          /* |G| = |V0| = |V1|                                                   */
+  int32_t delta;          /* |A| = |B|                                                           */
+  int32_t k_A, k_B;       /* dimensions of C_A and C_B                                           */
+  int32_t m_l[2];         /* local checks per vertex: k_A k_B (side 0), (D-k_A)(D-k_B) (side 1)  */
+  int32_t m[2];           /* global checks per side = order * m_l[side]                          */
+  int32_t rank[2];        /* GF(2) ranks of H_Z (side 0) and H_X (side 1)                        */
+  int32_t k;              /* logical qubits n - rank[0] - rank[1]                                */
+  int32_t words_n;        /* uint32 words per error / correction row                             */
+  int32_t words_m[2];     /* uint32 words per syndrome row of each side                          */
+  int32_t max_row_weight[2];
+  int32_t prepared_device;/* device the tables live on, or -1                                    */
+} lead_code_info;
+
+/* Options of one decode call on one side. */
+typedef struct {
+  int32_t side;           /* 0 or 1                                                              */
+  int32_t use_lead;       /* 1: Phases 1-3; 0: the standalone min-sum baseline on the channel prior */
+  int32_t max_iter;       /* global min-sum iterations, 0..64                                    */
+  int32_t precision;      /* LEAD_PREC_FP32                                                       */
+  float   alpha;          /* Phase-2 scaling, 0 < alpha <= 1 (Sec. III-B; 1 is the default)      */
+  double  p;              /* channel marginal of this side's error type, 0 < p < 1/2              */
+} lead_decode_opts;
+
+/*
+ * lead_build_code -- the quantum Tanner code of Sec. II from (G, A, B, C_A, C_B). Host only:
+ * no device is touched, so it also runs on machines without a GPU.
+ *  G     (host) Cayley table of the group, validated as a group table.
+ *  A, B  (host) delta element indices each; their order fixes the local coordinates. Checked:
+ *        A = A^{-1}, B = B^{-1}, no repeats, no identity (Sec. II-A) and Total No-Conjugacy
+ *        ag != gb for all a, b, g (Eq. group_set and the paragraph after it).
+ *  GA    (host) kA x delta row-major 0/1 bytes, a full-rank generator matrix of C_A.
+ *  GB    (host) kB x delta generator of C_B, or NULL for C_B = C_A^perp (the paper's choice in
+ *        every instance of Sec. IV and Appendix A); then kB is ignored.
+ * Readings fixed by the library (the paper leaves them open):
+ *  - the face of (g, a, b) is {(g,0),(ag,1),(gb,1),(agb,0)}; (g,a,b) and (agb,a^-1,b^-1) name the
+ *    same face and its qubit index is the rank of the lexicographically smaller tuple
+ *    (g, index(a), index(b)) among all faces;
+ *  - a V0 vertex g sees face (g,a,b) at local index j = index(b)*delta + index(a); a V1 vertex h
+ *    sees at j the face (a h, a^-1, b), i.e. {(h,1),(ah,0),(hb,0),(ahb,1)};
+ *  - local checks: side 0 the rows of kron(G_B, G_A), side 1 the rows of kron(H_B, H_A), where
+ *    H_A, H_B and a missing G_B are the reduced-row-echelon bases of the dual codes; global
+ *    check index = vertex * m_l + local row (so s_v is a contiguous m_l-bit field).
+ *  out   receives a new code object; release it with lead_free_code.
+ * Errors: LEAD_EINVAL (sizes; delta must be 2..6, at most 12 local rows per vertex on each side,
+ *        every check row weight at most 26),
+ * LEAD_ENOTGROUP, LEAD_ENOTSYM, LEAD_ENOTTNC, LEAD_ECSS, LEAD_EOOM.
+ */
+int lead_build_code(const lead_group* G, const int32_t* A, const int32_t* B, int32_t delta,
+                     const uint8_t* GA, int32_t kA, const uint8_t* GB, int32_t kB,
+                     lead_code** out);
+
+/* Fill *out with the code's sizes (host only). */
+int lead_code_get_info(const lead_code* code, lead_code_info* out);
+
+/* Copy the local views of one side: views[v * delta^2 + j] = qubit (host array of
+ * order * delta^2 int32). Host only; for inspection and tests. */
+int lead_code_get_views(const lead_code* code, int32_t side, int32_t* views);
+
+/* Copy one side's check matrix as m x n row-major 0/1 bytes (host). Host only. */
+int lead_code_get_check_matrix(const lead_code* code, int32_t side, uint8_t* H);
+
+/*
+ * lead_code_prepare -- upload the code's tables to `device` and compute, on that device, the
+ * exact local coset weight enumerators of both sides (the p-independent part of Phase 1:
+ * N_s[w] = number of local patterns of weight w with local syndrome s, N1_s[j][w] those with
+ * bit j set, and the least-weight member of every coset). Synchronises with the device before
+ * returning. Call once, before any stream capture; later calls on the same device return
+ * LEAD_OK at once. Errors: LEAD_ECUDA, LEAD_EOOM, LEAD_ESTATE (already prepared elsewhere).
+ */
+int lead_code_prepare(lead_code* code, int32_t device);
+
+/*
+ * lead_code_get_enumerators -- copy one side's device-computed enumerator tables to the host:
+ * N (2^m_l x (delta^2+1) int32), N1 (2^m_l x delta^2 x (delta^2+1) int32) and ml
+ * (2^m_l uint64, bit j = local index j of the least-weight coset member; ties broken by the
+ * least row-major key sum_{a,b} E[a][b] 2^(a*delta+b)). Any output may be NULL. Synchronous.
+ */
+int lead_code_get_enumerators(const lead_code* code, int32_t side, int32_t* N, int32_t* N1,
+                              uint64_t* ml);
+
+void lead_free_code(lead_code* code);
+
+/*
+ * lead_sample -- noise of Sec. IV-A and its syndromes, on the device.
+ *  noise        LEAD_NOISE_X, LEAD_NOISE_Z or LEAD_NOISE_DEPOL; 0 <= p < 1.
+ *  shots        rows to produce; shot_offset + row is the absolute shot index.
+ *  Random numbers: the uniform for qubit i of absolute shot s is word (i mod 4) of
+ *  Philox4x32-10 (Salmon et al., SC'11) with counter (i div 4, s mod 2^32, s div 2^32, 0) and
+ *  key (seed mod 2^32, seed div 2^32). A qubit flips (Bernoulli) iff u < floor(p 2^32); for
+ *  depolarizing, u < floor(p/3 2^32) is X, < floor(2p/3 2^32) is Y, < floor(p 2^32) is Z.
+ *  err_x, err_z (dev, shots x words_n) X and Z parts of the error; syn_z (dev, shots x
+ *  words_m[0]) = H_Z err_x; syn_x (dev, shots x words_m[1]) = H_X err_z. Any output may be
+ *  NULL (its part is then not written).
+ */
+int lead_sample(const lead_code* code, int32_t noise, double p, int64_t shots, uint64_t seed,
+                uint64_t shot_offset, uint32_t* err_x, uint32_t* err_z, uint32_t* syn_z,
+                uint32_t* syn_x, void* stream);
+
+/* Bytes of device workspace lead_local_estimate / lead_decode need for these options
+ * (16-byte aligned start required); 0 for the baseline (use_lead = 0). */
+size_t lead_workspace_bytes(const lead_code* code, const lead_decode_opts* opts, int64_t shots);
+
+/*
+ * lead_local_table -- Phase 1 for a uniform channel prior p, for every local syndrome:
+ * table[s * delta^2 + j] (dev, 2^m_l x delta^2 float) = binary32 rounding of the exact posterior
+ * q_{s,j} = P(e_j = 1 | H_v e = s) = N1_s,j(r) / N_s(r) with r = p/(1-p) (both polynomials
+ * evaluated in binary64 by Horner's rule), then max(q, 1/2) on the bits of the least-weight
+ * coset member (the confidence boost of Algorithm 1). 0 < p < 1/2.
+ */
+int lead_local_table(const lead_code* code, int32_t side, double p, float* table, void* stream);
+
+/*
+ * lead_local_estimate -- Phases 1 and 2 (Algorithm 1): for every qubit i with views (v0, j0)
+ * and (v1, j1) on the side, p_i = alpha * ((q(s_v0, j0) + q(s_v1, j1)) * 1/2) in binary32,
+ * clamped to [2^-23, 1 - 2^-23], and llr[shot * n + i] = ln((1 - p_i)/p_i) (binary32; the
+ * logarithm by the inverse-hyperbolic-tangent series, see the decode notes).
+ *  syn (dev, shots x words_m[side]); llr (dev, shots x n float);
+ *  workspace (dev) >= lead_workspace_bytes(opts), contents need not be initialised.
+ */
+int lead_local_estimate(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn,
+                        int64_t shots, float* llr, void* workspace, size_t ws_bytes,
+                        void* stream);
+
+/*
+ * lead_decode -- Algorithm 1 on one side for `shots` syndromes (or the standalone min-sum
+ * baseline when opts->use_lead == 0, which uses the channel LLR ln((1-p)/p) for every qubit).
+ *  syn    (dev, shots x words_m[side]) syndromes.
+ *  corr   (dev, shots x words_n) corrections (the last hard decision when not converged).
+ *  status (dev, shots uint8) LEAD_ST_* bits.
+ *  iters  (dev, shots int32, nullable) global iterations used (0 = the prior's own hard decision
+ *         already satisfied the syndrome).
+ *  llr    (dev, shots x n float, nullable) final posterior LLRs.
+ *  Global min-sum (the paper's global decoder uses BP with min-sum; OSD is not included):
+ *  flooding schedule, scaling 1, binary32 messages; c2v = (-1)^(s_c + #negative other v2c) *
+ *  min |other v2c|, v2c = post - c2v, post_i = (lambda_i + U_v0) + U_v1 with U_v the sum of the
+ *  messages from v's local rows in increasing row order (v0 < v1 the two views of qubit i),
+ *  hard decision e_i = [post_i < 0], stop at the first iteration whose decision satisfies
+ *  H e = s (iteration 0 tests the prior's decision).
+ * shots == 0 is a no-op (pointers may then be NULL).
+ * Errors: LEAD_EINVAL (including max_iter > 64 or alpha outside (0,1]; codes whose vertex count
+ *        times the shared memory of one shot exceed one CTA), LEAD_ESTATE, LEAD_ECUDA.
+ */
+int lead_decode(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn,
+                int64_t shots, uint32_t* corr, uint8_t* status, int32_t* iters, float* llr,
+                void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * lead_check -- success test of Sec. IV-A on one side: residual r = err + corr.
+ *  fail[shot] (dev uint8): bit 0 set iff H r != 0 (the correction misses the syndrome);
+ *  bit 1 set iff H r = 0 and r is a nontrivial logical operator (it anticommutes with one of
+ *  the code's logical operators of the other type, computed at build time by GF(2) elimination).
+ *  err, corr (dev, shots x words_n).
+ */
+int lead_check(const lead_code* code, int32_t side, const uint32_t* err, const uint32_t* corr,
+               int64_t shots, uint8_t* fail, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* lead_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEAD_H */

@@ -1,0 +1,277 @@
+// Device tables of a code, the exact local coset enumerators (Phase 1, p-independent part) and
+// the per-p local posterior table (Phase 1 + boost).
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "lead_device.cuh"
+
+namespace lead {
+
+int sm_count(int device) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+namespace {
+
+// Row-by-row dynamic programme over the Delta rows of the local view E (rows a, columns b,
+// local index j = b*Delta + a). A row pattern x (bit b = E[a][b]) adds contrib[a][x] to the
+// local syndrome. Run 0 counts all patterns per (syndrome, weight): N. Run 1 + j counts those
+// with bit j set, by admitting at row a = j mod Delta only patterns with bit b = j div Delta.
+// State counts stay below 2^36 (64-bit accumulators); final entries are at most 2^(nl - m_l).
+__global__ void enumerate_kernel(int delta, int m_l, const uint16_t* __restrict__ contrib,
+                                 unsigned long long* __restrict__ bufs, int32_t* __restrict__ N,
+                                 int32_t* __restrict__ N1) {
+  const int run = blockIdx.x;
+  const int nl = delta * delta;
+  const int W = nl + 1;
+  const int states = 1 << m_l;
+  const size_t sz = (size_t)states * W;
+  unsigned long long* cur = bufs + (size_t)run * 2 * sz;
+  unsigned long long* nxt = cur + sz;
+  for (size_t i = threadIdx.x; i < sz; i += blockDim.x) cur[i] = (i == 0) ? 1ull : 0ull;
+  __syncthreads();
+  const int fj = run - 1;
+  for (int a = 0; a < delta; ++a) {
+    const int forced_b = (fj >= 0 && fj % delta == a) ? fj / delta : -1;
+    const uint16_t* ca = contrib + a * (1 << delta);
+    for (size_t i = threadIdx.x; i < sz; i += blockDim.x) {
+      const int S = (int)(i / W), w = (int)(i % W);
+      unsigned long long acc = 0;
+      for (int x = 0; x < (1 << delta); ++x) {
+        if (forced_b >= 0 && !((x >> forced_b) & 1)) continue;
+        const int wx = __popc(x);
+        if (wx > w) continue;
+        acc += cur[(size_t)(S ^ ca[x]) * W + (w - wx)];
+      }
+      nxt[i] = acc;
+    }
+    __syncthreads();
+    unsigned long long* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  for (size_t i = threadIdx.x; i < sz; i += blockDim.x) {
+    const int S = (int)(i / W), w = (int)(i % W);
+    const int32_t val = (int32_t)cur[i];
+    if (run == 0) N[i] = val;
+    else N1[((size_t)S * nl + fj) * W + w] = val;
+  }
+}
+
+// Least (weight, row-major key) member of every coset by the same row recursion in the
+// (min, +) semiring: key = sum_a x_a 2^(a*Delta), packed with the weight as weight<<40 | key;
+// comparing packed values compares (weight, key) lexicographically, and the order of partial
+// solutions reaching a state is preserved by any common completion.
+__global__ void ml_kernel(int delta, int m_l, const uint16_t* __restrict__ contrib,
+                          unsigned long long* __restrict__ buf, uint64_t* __restrict__ ml) {
+  const int states = 1 << m_l;
+  unsigned long long* cur = buf;
+  unsigned long long* nxt = buf + states;
+  const unsigned long long INF = ~0ull;
+  for (int S = threadIdx.x; S < states; S += blockDim.x) cur[S] = (S == 0) ? 0ull : INF;
+  __syncthreads();
+  for (int a = 0; a < delta; ++a) {
+    const uint16_t* ca = contrib + a * (1 << delta);
+    for (int S = threadIdx.x; S < states; S += blockDim.x) {
+      unsigned long long best = INF;
+      for (int x = 0; x < (1 << delta); ++x) {
+        const unsigned long long prev = cur[S ^ ca[x]];
+        if (prev == INF) continue;
+        const unsigned long long cand =
+            prev + ((unsigned long long)__popc(x) << 40) + ((unsigned long long)x << (a * delta));
+        best = cand < best ? cand : best;
+      }
+      nxt[S] = best;
+    }
+    __syncthreads();
+    unsigned long long* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  for (int S = threadIdx.x; S < states; S += blockDim.x) {
+    const unsigned long long key = cur[S] & ((1ull << 40) - 1);
+    uint64_t mask = 0;
+    for (int a = 0; a < delta; ++a)
+      for (int b = 0; b < delta; ++b)
+        if ((key >> (a * delta + b)) & 1) mask |= 1ull << (b * delta + a);
+    ml[S] = cur[S] == INF ? ~0ull : mask;
+  }
+}
+
+// q[s][j] = N1_s,j(r) / N_s(r), both by Horner from the highest degree with separate binary64
+// multiply and add (no fused multiply-add), rounded to binary32; then max(q, 1/2) on the bits
+// of the least-weight coset member.
+__global__ void table_kernel(int nl, int m_l, double r, const int32_t* __restrict__ N,
+                             const int32_t* __restrict__ N1, const uint64_t* __restrict__ ml,
+                             float* __restrict__ table) {
+  const int W = nl + 1;
+  const int total = (1 << m_l) * nl;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int s = i / nl, j = i - s * nl;
+    double num = 0.0, den = 0.0;
+    for (int w = nl; w >= 0; --w) {
+      num = __dadd_rn(__dmul_rn(num, r), (double)N1[((size_t)s * nl + j) * W + w]);
+      den = __dadd_rn(__dmul_rn(den, r), (double)N[(size_t)s * W + w]);
+    }
+    float q = __double2float_rn(__ddiv_rn(num, den));
+    if ((ml[s] >> j) & 1) q = fmaxf(q, 0.5f);
+    table[i] = q;
+  }
+}
+
+template <typename T>
+int upload(T** dst, const std::vector<T>& src) {
+  if (src.empty()) {
+    *dst = nullptr;
+    return LEAD_OK;
+  }
+  if (cudaMalloc(dst, src.size() * sizeof(T)) != cudaSuccess) return LEAD_EOOM;
+  LEAD_CUDA_TRY(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return LEAD_OK;
+}
+
+#define LEAD_TRY(expr)             \
+  do {                             \
+    int _rc = (expr);              \
+    if (_rc != LEAD_OK) return _rc; \
+  } while (0)
+
+int prepare_side(lead_code* code, int s) {
+  HostSide& hs = code->side[s];
+  DeviceSide& ds = code->dside[s];
+  const int nl = code->nl, delta = code->delta;
+  std::vector<uint16_t> views(hs.views.begin(), hs.views.end());
+  LEAD_TRY(upload(&ds.views, views));
+  LEAD_TRY(upload(&ds.partner, hs.partner));
+  LEAD_TRY(upload(&ds.qslots, hs.qslots));
+  LEAD_TRY(upload(&ds.logicals, hs.logicals));
+  // syndrome contribution of row pattern x at row a: bit (rB*kRA + rA) = RA[rA][a] * (RB x)[rB]
+  std::vector<uint16_t> contrib((size_t)delta << delta, 0);
+  for (int a = 0; a < delta; ++a)
+    for (int x = 0; x < (1 << delta); ++x) {
+      uint32_t c = 0;
+      for (int rB = 0; rB < hs.kRB; ++rB) {
+        int f = 0;
+        for (int b = 0; b < delta; ++b) f ^= ((x >> b) & 1) & hs.RB[rB * delta + b];
+        if (!f) continue;
+        for (int rA = 0; rA < hs.kRA; ++rA)
+          if (hs.RA[rA * delta + a]) c ^= 1u << (rB * hs.kRA + rA);
+      }
+      contrib[(size_t)a * (1 << delta) + x] = (uint16_t)c;
+    }
+  uint16_t* dcontrib = nullptr;
+  LEAD_TRY(upload(&dcontrib, contrib));
+  const int states = 1 << hs.m_l;
+  const size_t sz = (size_t)states * (nl + 1);
+  if (cudaMalloc(&ds.enumN, sz * sizeof(int32_t)) != cudaSuccess) return LEAD_EOOM;
+  if (cudaMalloc(&ds.enumN1, sz * nl * sizeof(int32_t)) != cudaSuccess) return LEAD_EOOM;
+  if (cudaMalloc(&ds.ml, states * sizeof(uint64_t)) != cudaSuccess) return LEAD_EOOM;
+  unsigned long long* bufs = nullptr;
+  // (nl + 1) double-buffered enumeration runs, then the two buffers of the ML recursion
+  const size_t nbuf = sz * 2 * (nl + 1) + (size_t)states * 2;
+  if (cudaMalloc(&bufs, nbuf * sizeof(unsigned long long)) != cudaSuccess) {
+    cudaFree(dcontrib);
+    return LEAD_EOOM;
+  }
+  enumerate_kernel<<<nl + 1, 512>>>(delta, hs.m_l, dcontrib, bufs, ds.enumN, ds.enumN1);
+  cudaError_t e1 = cudaGetLastError();
+  ml_kernel<<<1, 512>>>(delta, hs.m_l, dcontrib, bufs + sz * 2 * (nl + 1), ds.ml);
+  cudaError_t e2 = cudaGetLastError();
+  cudaError_t e3 = cudaDeviceSynchronize();
+  cudaFree(bufs);
+  cudaFree(dcontrib);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return LEAD_ECUDA;
+  return LEAD_OK;
+}
+
+}  // namespace
+
+int prepare_device(lead_code* code, int device) {
+  if (code->device == device) return LEAD_OK;
+  if (code->device >= 0) return LEAD_ESTATE;
+  LEAD_CUDA_TRY(cudaSetDevice(device));
+  code->device = device;
+  for (int s = 0; s < 2; ++s) {
+    int rc = prepare_side(code, s);
+    if (rc != LEAD_OK) {
+      release_device(code);
+      return rc;
+    }
+  }
+  return LEAD_OK;
+}
+
+void release_device(lead_code* code) {
+  if (code->device < 0) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(code->device);
+  for (auto& ds : code->dside) {
+    cudaFree(ds.views);
+    cudaFree(ds.partner);
+    cudaFree(ds.qslots);
+    cudaFree(ds.enumN);
+    cudaFree(ds.enumN1);
+    cudaFree(ds.ml);
+    cudaFree(ds.logicals);
+    ds = DeviceSide{};
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  code->device = -1;
+}
+
+int check_device(const lead_code* code) {
+  if (!code) return LEAD_EINVAL;
+  if (code->device < 0) return LEAD_ESTATE;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return LEAD_ECUDA;
+  return cur == code->device ? LEAD_OK : LEAD_ESTATE;
+}
+
+int launch_table(const lead_code* code, int side, double p, float* table, cudaStream_t stream) {
+  if (!(p > 0.0 && p < 0.5)) return LEAD_EINVAL;
+  const HostSide& hs = code->side[side];
+  const DeviceSide& ds = code->dside[side];
+  const double r = p / (1.0 - p);
+  const int total = (1 << hs.m_l) * code->nl;
+  const int threads = 256;
+  const int blocks = (total + threads - 1) / threads;
+  table_kernel<<<blocks, threads, 0, stream>>>(code->nl, hs.m_l, r, ds.enumN, ds.enumN1, ds.ml, table);
+  LEAD_CUDA_TRY(cudaGetLastError());
+  return LEAD_OK;
+}
+
+}  // namespace lead
+
+extern "C" {
+
+int lead_code_prepare(lead_code* code, int32_t device) {
+  if (!code || device < 0) return LEAD_EINVAL;
+  return lead::prepare_device(code, device);
+}
+
+int lead_code_get_enumerators(const lead_code* code, int32_t side, int32_t* N, int32_t* N1,
+                              uint64_t* ml) {
+  if (!code || side < 0 || side > 1) return LEAD_EINVAL;
+  if (code->device < 0) return LEAD_ESTATE;
+  const auto& hs = code->side[side];
+  const auto& ds = code->dside[side];
+  const size_t sz = (size_t)(1 << hs.m_l) * (code->nl + 1);
+  if (N) LEAD_CUDA_TRY(cudaMemcpy(N, ds.enumN, sz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (N1) LEAD_CUDA_TRY(cudaMemcpy(N1, ds.enumN1, sz * code->nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (ml) LEAD_CUDA_TRY(cudaMemcpy(ml, ds.ml, (size_t)(1 << hs.m_l) * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  return LEAD_OK;
+}
+
+int lead_local_table(const lead_code* code, int32_t side, double p, float* table, void* stream) {
+  if (!code || !table || side < 0 || side > 1) return LEAD_EINVAL;
+  int rc = lead::check_device(code);
+  if (rc != LEAD_OK) return rc;
+  return lead::launch_table(code, side, p, table, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Internal definitions shared by the host construction (code.cpp) and the CUDA translation
+// units of the LEAD library. Not part of the public ABI (include/lead.h is).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/lead.h"
+
+namespace lead {
+
+constexpr int kMaxDelta = 6;          // local views of at most 36 qubits (64-bit masks)
+constexpr int kMaxLocalRows = 12;     // m_l <= 12 local checks per vertex (2^m_l-entry tables)
+constexpr int kMaxSupport = 26;       // local check rows of weight <= 26 (packed sign bits)
+constexpr int kMaxIter = 64;
+
+// Per-side structure that kernels receive by value.
+struct SideParams {
+  int32_t order;          // vertices of the side (= |G|)
+  int32_t nl;             // delta^2
+  int32_t m_l;            // local rows per vertex
+  int32_t m;              // global checks
+  int32_t words_m;        // syndrome words per shot
+  int32_t supp_len[kMaxLocalRows];
+  uint8_t supp[kMaxLocalRows][kMaxSupport];   // local indices j of row r, increasing
+  uint64_t rowmask[kMaxLocalRows];            // bit j set iff row r touches local index j
+};
+
+struct DeviceSide {
+  uint16_t* views = nullptr;     // order*nl qubit ids
+  uint32_t* partner = nullptr;   // order*nl: (other slot) | (this view is the first << 31)
+  uint32_t* qslots = nullptr;    // n*2: slot of the qubit's first view, second view
+  int32_t* enumN = nullptr;      // 2^m_l x (nl+1)
+  int32_t* enumN1 = nullptr;     // 2^m_l x nl x (nl+1)
+  uint64_t* ml = nullptr;        // 2^m_l least-weight coset members
+  uint32_t* logicals = nullptr;  // k x words_n
+};
+
+struct HostSide {
+  int32_t m_l = 0;
+  int32_t m = 0;
+  int32_t rank = 0;
+  int32_t max_row_weight = 0;
+  std::vector<uint64_t> rowmask;     // m_l
+  std::vector<int32_t> views;        // order*nl
+  std::vector<uint32_t> partner;     // order*nl
+  std::vector<uint32_t> qslots;      // n*2
+  std::vector<uint32_t> logicals;    // k*words_n (operators of the other type)
+  std::vector<uint8_t> RA, RB;       // row factors: local checks = kron(RB, RA)
+  int32_t kRA = 0, kRB = 0;
+  SideParams params{};
+};
+
+}  // namespace lead
+
+struct lead_code {
+  int32_t order = 0, delta = 0, nl = 0, kA = 0, kB = 0, n = 0, k = 0, words_n = 0;
+  std::vector<int32_t> mul, inv;
+  int32_t identity = -1;
+  std::vector<int32_t> A, B;
+  std::vector<uint8_t> GA, GB, HA, HB;    // row-major, delta columns
+  lead::HostSide side[2];
+  int32_t device = -1;
+  lead::DeviceSide dside[2];
+};
+
+namespace lead {
+// Implemented in the CUDA translation units.
+int prepare_device(lead_code* code, int device);
+void release_device(lead_code* code);
+}  // namespace lead

@@ -1,0 +1,230 @@
+"""Thin Python binding of the LEAD C ABI (include/lead.h): argument marshalling only.
+
+Every computation runs in liblead.so; this module loads it with ctypes, passes torch tensors'
+device pointers and the current CUDA stream, and raises on any non-zero status. There is no
+fallback: if the library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblead.so")
+
+NOISE_X, NOISE_Z, NOISE_DEPOL = 0, 1, 2
+ST_CONVERGED, ST_MAX_ITER = 1, 2
+PREC_FP32 = 0
+
+_c_int32_p = ctypes.POINTER(ctypes.c_int32)
+_c_uint8_p = ctypes.POINTER(ctypes.c_uint8)
+
+
+class LeadGroup(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("mul", _c_int32_p)]
+
+
+class LeadCodeInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("order", ctypes.c_int32), ("delta", ctypes.c_int32),
+                ("k_A", ctypes.c_int32), ("k_B", ctypes.c_int32),
+                ("m_l", ctypes.c_int32 * 2), ("m", ctypes.c_int32 * 2), ("rank", ctypes.c_int32 * 2),
+                ("k", ctypes.c_int32), ("words_n", ctypes.c_int32), ("words_m", ctypes.c_int32 * 2),
+                ("max_row_weight", ctypes.c_int32 * 2), ("prepared_device", ctypes.c_int32)]
+
+
+class LeadDecodeOpts(ctypes.Structure):
+    _fields_ = [("side", ctypes.c_int32), ("use_lead", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("alpha", ctypes.c_float), ("p", ctypes.c_double)]
+
+
+EXPORTS = {
+    "lead_build_code": (ctypes.c_int, [ctypes.POINTER(LeadGroup), _c_int32_p, _c_int32_p, ctypes.c_int32,
+                                       _c_uint8_p, ctypes.c_int32, _c_uint8_p, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "lead_code_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadCodeInfo)]),
+    "lead_code_get_views": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _c_int32_p]),
+    "lead_code_get_check_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _c_uint8_p]),
+    "lead_code_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "lead_code_get_enumerators": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _c_int32_p, _c_int32_p,
+                                                 ctypes.POINTER(ctypes.c_uint64)]),
+    "lead_free_code": (None, [ctypes.c_void_p]),
+    "lead_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int64,
+                                   ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lead_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_int64]),
+    "lead_local_table": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "lead_local_estimate": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_void_p,
+                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                           ctypes.c_void_p]),
+    "lead_decode": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_void_p,
+                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "lead_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    "lead_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"liblead.so is not built ({LIB_PATH}); run `python -m paper_2605_17796_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+class LeadError(RuntimeError):
+    def __init__(self, call: str, rc: int):
+        super().__init__(f"{call} failed: {rc} ({LIB.lead_status_string(rc).decode()})")
+        self.rc = rc
+
+
+def _check(call: str, rc: int):
+    if rc != 0:
+        raise LeadError(call, rc)
+
+
+def _ptr(t) -> int | None:
+    """Device pointer of a CUDA tensor (None for None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int | None:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+@dataclass
+class CodeInfo:
+    n: int
+    order: int
+    delta: int
+    k_A: int
+    k_B: int
+    m_l: tuple
+    m: tuple
+    rank: tuple
+    k: int
+    words_n: int
+    words_m: tuple
+    max_row_weight: tuple
+    prepared_device: int
+
+
+class Code:
+    """A quantum Tanner code built by the library from (G, A, B, C_A[, C_B])."""
+
+    def __init__(self, mul: np.ndarray, A, B, GA: np.ndarray, GB: np.ndarray | None = None):
+        mul = np.ascontiguousarray(mul, dtype=np.int32)
+        A = np.ascontiguousarray(A, dtype=np.int32)
+        B = np.ascontiguousarray(B, dtype=np.int32)
+        GA = np.ascontiguousarray(GA, dtype=np.uint8)
+        grp = LeadGroup(order=mul.shape[0], mul=mul.ctypes.data_as(_c_int32_p))
+        out = ctypes.c_void_p()
+        gb_p = None
+        kB = 0
+        if GB is not None:
+            GB = np.ascontiguousarray(GB, dtype=np.uint8)
+            gb_p = GB.ctypes.data_as(_c_uint8_p)
+            kB = GB.shape[0]
+        rc = LIB.lead_build_code(ctypes.byref(grp), A.ctypes.data_as(_c_int32_p), B.ctypes.data_as(_c_int32_p),
+                                 len(A), GA.ctypes.data_as(_c_uint8_p), GA.shape[0], gb_p, kB, ctypes.byref(out))
+        _check("lead_build_code", rc)
+        self._h = out
+        self.info = self._info()
+
+    @classmethod
+    def from_instance(cls, inst) -> "Code":
+        G = inst.G
+        return cls(G.mul, inst.A, inst.B, inst.GA, inst.GB)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            LIB.lead_free_code(h)
+            self._h = None
+
+    def _info(self) -> CodeInfo:
+        ci = LeadCodeInfo()
+        _check("lead_code_get_info", LIB.lead_code_get_info(self._h, ctypes.byref(ci)))
+        return CodeInfo(ci.n, ci.order, ci.delta, ci.k_A, ci.k_B, tuple(ci.m_l), tuple(ci.m), tuple(ci.rank),
+                        ci.k, ci.words_n, tuple(ci.words_m), tuple(ci.max_row_weight), ci.prepared_device)
+
+    def views(self, side: int) -> np.ndarray:
+        out = np.zeros((self.info.order, self.info.delta ** 2), dtype=np.int32)
+        _check("lead_code_get_views", LIB.lead_code_get_views(self._h, side, out.ctypes.data_as(_c_int32_p)))
+        return out
+
+    def check_matrix(self, side: int) -> np.ndarray:
+        out = np.zeros((self.info.m[side], self.info.n), dtype=np.uint8)
+        _check("lead_code_get_check_matrix",
+               LIB.lead_code_get_check_matrix(self._h, side, out.ctypes.data_as(_c_uint8_p)))
+        return out
+
+    def prepare(self, device: int = 0) -> "Code":
+        _check("lead_code_prepare", LIB.lead_code_prepare(self._h, device))
+        self.info = self._info()
+        return self
+
+    def enumerators(self, side: int):
+        i = self.info
+        nl = i.delta ** 2
+        S = 1 << i.m_l[side]
+        N = np.zeros((S, nl + 1), dtype=np.int32)
+        N1 = np.zeros((S, nl, nl + 1), dtype=np.int32)
+        ml = np.zeros(S, dtype=np.uint64)
+        _check("lead_code_get_enumerators", LIB.lead_code_get_enumerators(
+            self._h, side, N.ctypes.data_as(_c_int32_p), N1.ctypes.data_as(_c_int32_p),
+            ml.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return N, N1, ml
+
+    # ---- device calls (torch tensors in, enqueued on the current stream) --------------------
+
+    def sample(self, noise: int, p: float, shots: int, seed: int, shot_offset: int = 0,
+               err_x=None, err_z=None, syn_z=None, syn_x=None, stream=None):
+        _check("lead_sample", LIB.lead_sample(self._h, noise, p, shots, seed, shot_offset, _ptr(err_x),
+                                              _ptr(err_z), _ptr(syn_z), _ptr(syn_x), _stream(stream)))
+
+    def workspace_bytes(self, opts: LeadDecodeOpts, shots: int = 0) -> int:
+        return int(LIB.lead_workspace_bytes(self._h, ctypes.byref(opts), shots))
+
+    def local_table(self, side: int, p: float, table, stream=None):
+        _check("lead_local_table", LIB.lead_local_table(self._h, side, p, _ptr(table), _stream(stream)))
+
+    def local_estimate(self, opts: LeadDecodeOpts, syn, shots: int, llr, workspace, stream=None):
+        ws = _ptr(workspace)
+        nb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        _check("lead_local_estimate", LIB.lead_local_estimate(self._h, ctypes.byref(opts), _ptr(syn), shots,
+                                                              _ptr(llr), ws, nb, _stream(stream)))
+
+    def decode(self, opts: LeadDecodeOpts, syn, shots: int, corr, status, iters=None, llr=None,
+               workspace=None, stream=None):
+        ws = _ptr(workspace)
+        nb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        _check("lead_decode", LIB.lead_decode(self._h, ctypes.byref(opts), _ptr(syn), shots, _ptr(corr),
+                                              _ptr(status), _ptr(iters), _ptr(llr), ws, nb, _stream(stream)))
+
+    def check(self, side: int, err, corr, shots: int, fail, stream=None):
+        _check("lead_check", LIB.lead_check(self._h, side, _ptr(err), _ptr(corr), shots, _ptr(fail),
+                                            _stream(stream)))
+
+
+def opts(side: int = 0, p: float = 0.05, alpha: float = 1.0, max_iter: int = 32, use_lead: bool = True,
+         precision: int = PREC_FP32) -> LeadDecodeOpts:
+    return LeadDecodeOpts(side=side, use_lead=1 if use_lead else 0, max_iter=max_iter, precision=precision,
+                          alpha=alpha, p=p)

@@ -1,0 +1,85 @@
+"""CPU tests of the C ABI: the library loads, exports every declared symbol, and its host-side
+code construction matches the oracle's (no device calls)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import tanner
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lead():
+    from paper_2605_17796_gb300 import build as b
+    if not os.path.exists(b.LIB):
+        b.build()
+    from paper_2605_17796_gb300 import lead as L
+    return L
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "lead.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lead_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lead):
+    names = _declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lead.LIB, name), name
+        assert name in lead.EXPORTS, f"binding lacks {name}"
+
+
+@pytest.mark.parametrize("name", ["SL(2,3)", "PSL(2,7)"])
+def test_host_construction_matches_oracle(lead, name):
+    inst = workloads.standard(name, 0)
+    code = lead.Code.from_instance(inst)
+    oc = tanner.from_instance(inst)
+    assert code.info.n == oc.n and code.info.k == oc.k
+    assert code.info.rank == (oc.rank_HZ, oc.rank_HX)
+    for s in (0, 1):
+        assert (code.views(s) == oc.sides[s].views).all()
+        assert (code.check_matrix(s) == oc.sides[s].H).all()
+        assert code.info.m_l[s] == oc.sides[s].m_l
+    assert code.info.prepared_device == -1
+
+
+def test_paper_local_code_matches_oracle(lead):
+    inst = workloads.paper_instance("PSL(2,7)")
+    code = lead.Code.from_instance(inst)
+    oc = tanner.from_instance(inst)
+    for s in (0, 1):
+        assert (code.check_matrix(s) == oc.sides[s].H).all()
+
+
+def test_error_codes(lead):
+    inst = workloads.standard("SL(2,3)", 0)
+    G = inst.G
+    with pytest.raises(lead.LeadError) as e:
+        lead.Code(G.mul, inst.A, inst.A, inst.GA)          # B = A: classes shared, TNC fails
+    assert e.value.rc == -2
+    A = list(inst.A)
+    A[0] = G.identity
+    with pytest.raises(lead.LeadError) as e:
+        lead.Code(G.mul, A, inst.B, inst.GA)
+    assert e.value.rc == -3
+    bad = G.mul.copy()
+    bad[0, 0], bad[0, 1] = bad[0, 1], bad[0, 0]
+    with pytest.raises(lead.LeadError) as e:
+        lead.Code(bad, inst.A, inst.B, inst.GA)
+    assert e.value.rc == -9
+    with pytest.raises(lead.LeadError) as e:
+        lead.Code(G.mul, inst.A, inst.B, np.zeros((2, 4), dtype=np.uint8))
+    assert e.value.rc == -1
+
+
+def test_device_calls_refuse_unprepared_code(lead):
+    inst = workloads.standard("SL(2,3)", 0)
+    code = lead.Code.from_instance(inst)
+    rc = lead.LIB.lead_check(code._h, 0, None, None, 0, None, None)
+    assert rc == -8          # LEAD_ESTATE: no device tables
