@@ -79,40 +79,43 @@ struct BPArgs {
   int32_t* iters;
   float* llr;
   const float* table;
-  const uint32_t* partner;
+  const uint16_t* pa;
   const uint16_t* views;
 };
 
-// Global min-sum for one group of `spb` shots per CTA, one thread per (shot, vertex).
-// Shared memory per shot: U[v][j] (sum of the messages of v's local rows into slot j),
-// post[v][j] (posterior LLR of slot j), and the compressed state of every check:
-// (min1, min2, meta) with meta bits 0..25 = signs of v2c by support position, 26..30 = position
-// of the first minimum, 31 = parity s_c + sum of signs. A message to position k is
-// (-1)^(parity + sign_k) * (k == argmin ? min2 : min1), i.e. exactly the min over the others.
 constexpr int kBPMaxThreads = 256;
 
-template <int NL>
-__global__ void __launch_bounds__(kBPMaxThreads)
+// Global min-sum for one group of `spb` shots per CTA, one thread per (shot, vertex).
+// Shared memory is slot-major with a compile-time row stride TS = spb * |V|: entry (j, t)
+// belongs to local index j of thread t (thread t = shot sl * V + vertex v of the group), so the
+// threads of a warp touch consecutive words and every own-slot offset is an immediate.
+//   U[j][t]    sum of the messages of the vertex's local rows into its slot j,
+//   post[j][t] posterior LLR of the slot,  lam[j][t] prior LLR of the slot.
+// A per-code global table pa[j][t] (16 bits, read through L1) holds the shared-memory address of
+// the partner slot (the other view of the same qubit), with bit 15 set when this view belongs
+// to the smaller vertex.
+// Each thread keeps the compressed state of its ML local checks in registers:
+// (min1, min2, meta) with meta bits 0..25 = signs of the v2c messages by support position,
+// 26..30 = position of the first minimum, 31 = parity s_c + sum of signs. The message to
+// position k is (-1)^(parity + sign_k) times (k == argmin ? min2 : min1), i.e. exactly the
+// minimum over the other positions.
+template <int NL, int ML, int TS>
+__global__ void __launch_bounds__((TS + 31) / 32 * 32, 3)
 bp_kernel(BPArgs a, __grid_constant__ const SideParams P) {
   extern __shared__ __align__(16) uint32_t smem[];
-  const int V = P.order, ml = P.m_l, spb = a.spb, wm = P.words_m;
-  float* U = reinterpret_cast<float*>(smem);
-  float* post_s = U + spb * V * NL;
-  uint32_t* S = reinterpret_cast<uint32_t*>(post_s + spb * V * NL);
-  uint32_t* syn_s = S + spb * V * ml * 3;
+  const int V = P.order, spb = a.spb, wm = P.words_m;
+  float* Us = reinterpret_cast<float*>(smem);
+  float* Ps = Us + NL * TS;
+  float* Ls = Ps + NL * TS;
+  uint32_t* syn_s = reinterpret_cast<uint32_t*>(Ls + NL * TS);
+  const uint16_t* __restrict__ PA = a.pa;          // [j][t]: partner address | first << 15
   uint32_t* cb = syn_s + spb * wm;
   int* flags = reinterpret_cast<int*>(cb + spb * a.words_n);
 
   const int tid = threadIdx.x;
   const int sl = tid / V, v = tid - sl * V;
-  const bool lane_ok = sl < spb;
-  uint32_t part[NL];
-#pragma unroll
-  for (int j = 0; j < NL; ++j) part[j] = lane_ok ? __ldg(a.partner + v * NL + j) : 0u;
+  const bool lane_ok = tid < TS;
   const float lam_ch = a.use_lead ? 0.0f : channel_llr(a.p);
-  const int shot_slots = sl * V * NL;
-  const int own = shot_slots + v * NL;
-  uint32_t* st_base = S + (size_t)(sl * V + v) * ml * 3;
 
   for (int64_t g0 = (int64_t)blockIdx.x * spb; g0 < a.shots; g0 += (int64_t)gridDim.x * spb) {
     const int nsh = (int)rows_left(spb, a.shots - g0);
@@ -121,45 +124,50 @@ bp_kernel(BPArgs a, __grid_constant__ const SideParams P) {
     if (tid < 2 * spb) flags[tid] = 0;
     __syncthreads();
     const bool act = lane_ok && sl < nsh;
-    float lam[NL];
+    float m1[ML], m2[ML];
+    uint32_t meta[ML];
+#pragma unroll
+    for (int r = 0; r < ML; ++r) {
+      m1[r] = 0.0f;
+      m2[r] = 0.0f;
+      meta[r] = 0u;
+    }
     uint32_t sv = 0;
     if (act) {
       const uint32_t* srow = syn_s + sl * wm;
-      sv = bit_field(srow, v * ml, ml);
-#pragma unroll
+      sv = bit_field(srow, v * ML, ML);
+#pragma unroll 2
       for (int j = 0; j < NL; ++j) {
         if (a.use_lead) {
-          const uint32_t ps = part[j] & 0x7FFFFFFFu;
-          const uint32_t vp = ps / NL, jp = ps - vp * NL;
-          const uint32_t svp = bit_field(srow, vp * ml, ml);
-          lam[j] = merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp), a.alpha);
+          const uint32_t addr = __ldg(PA + j * TS + tid) & 0x7FFFu;
+          const uint32_t jp = addr / TS, vp = addr - jp * TS - sl * V;
+          const uint32_t svp = bit_field(srow, vp * ML, ML);
+          Ls[j * TS + tid] = merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp), a.alpha);
         } else {
-          lam[j] = lam_ch;
+          Ls[j * TS + tid] = lam_ch;
         }
-        U[own + j] = 0.0f;
+        Us[j * TS + tid] = 0.0f;
       }
-      for (int i = 0; i < ml * 3; ++i) st_base[i] = 0u;
-    } else {
-#pragma unroll
-      for (int j = 0; j < NL; ++j) lam[j] = 0.0f;
     }
     __syncthreads();
     bool mydone = !act;
     for (int t = 0;; ++t) {
       uint64_t hm = 0;
       if (!mydone) {
-#pragma unroll
+#pragma unroll 4
         for (int j = 0; j < NL; ++j) {
-          const uint32_t ps = part[j];
-          const float up = U[shot_slots + (ps & 0x7FFFFFFFu)];
-          const float uo = U[own + j];
-          const float pj = (ps >> 31) ? __fadd_rn(__fadd_rn(lam[j], uo), up)
-                                      : __fadd_rn(__fadd_rn(lam[j], up), uo);
-          post_s[own + j] = pj;
+          const uint32_t pa = __ldg(PA + j * TS + tid);
+          const float up = Us[pa & 0x7FFFu];
+          const float uo = Us[j * TS + tid];
+          const float lj = Ls[j * TS + tid];
+          const float pj = (pa >> 15) ? __fadd_rn(__fadd_rn(lj, uo), up)
+                                      : __fadd_rn(__fadd_rn(lj, up), uo);
+          Ps[j * TS + tid] = pj;
           hm |= (uint64_t)(pj < 0.0f) << j;
         }
         uint32_t bad = 0;
-        for (int r = 0; r < ml; ++r) bad |= (uint32_t)(__popcll(hm & P.rowmask[r]) ^ (sv >> r)) & 1u;
+#pragma unroll
+        for (int r = 0; r < ML; ++r) bad |= (uint32_t)(__popcll(hm & P.rowmask[r]) ^ (sv >> r)) & 1u;
         if (bad) atomicOr(flags + (t & 1) * spb + sl, 1);
       }
       if (tid < spb) flags[((t + 1) & 1) * spb + tid] = 0;
@@ -168,12 +176,11 @@ bp_kernel(BPArgs a, __grid_constant__ const SideParams P) {
         const bool conv = flags[(t & 1) * spb + sl] == 0;
         if (conv || t >= a.max_iter) {
           const int64_t shot = g0 + sl;
-#pragma unroll
           for (int j = 0; j < NL; ++j) {
-            if (part[j] >> 31) {
+            if (__ldg(PA + j * TS + tid) >> 15) {
               const int q = __ldg(a.views + v * NL + j);
               if ((hm >> j) & 1) atomicOr(cb + sl * a.words_n + (q >> 5), 1u << (q & 31));
-              if (a.llr) a.llr[shot * a.n + q] = post_s[own + j];
+              if (a.llr) a.llr[shot * a.n + q] = Ps[j * TS + tid];
             }
           }
           if (v == 0) {
@@ -185,42 +192,45 @@ bp_kernel(BPArgs a, __grid_constant__ const SideParams P) {
       }
       if (!__syncthreads_or(!mydone)) break;
       if (!mydone) {
+#pragma unroll 4
+        for (int j = 0; j < NL; ++j) Us[j * TS + tid] = 0.0f;
 #pragma unroll
-        for (int j = 0; j < NL; ++j) U[own + j] = 0.0f;
-        for (int r = 0; r < ml; ++r) {
-          uint32_t* st = st_base + r * 3;
-          const float m1o = __uint_as_float(st[0]), m2o = __uint_as_float(st[1]);
-          const uint32_t mo = st[2];
+        for (int r = 0; r < ML; ++r) {
+          const float m1o = m1[r], m2o = m2[r];
+          const uint32_t mo = meta[r];
           const int amo = (int)((mo >> 26) & 31u);
-          const uint32_t paro = mo >> 31;
+          // bit k of `flip` = sign of the old message to position k (parity + sign_k)
+          uint32_t flip = mo ^ (0u - (mo >> 31));
           const int len = P.supp_len[r];
-          float m1 = __int_as_float(0x7F800000), m2 = __int_as_float(0x7F800000);
+          float n1 = __int_as_float(0x7F800000), n2 = __int_as_float(0x7F800000);
           int am = 0;
           uint32_t sg = 0;
           for (int k = 0; k < len; ++k) {
-            const int j = P.supp[r][k];
             const float mago = (k == amo) ? m2o : m1o;
-            const float co = ((paro ^ (mo >> k)) & 1u) ? -mago : mago;
-            const float v2c = __fsub_rn(post_s[own + j], co);
+            const float co = __uint_as_float(__float_as_uint(mago) ^ (flip << 31));
+            flip >>= 1;
+            const float v2c = __fsub_rn(Ps[P.supp[r][k] * TS + tid], co);
             const float m = fabsf(v2c);
-            sg |= (uint32_t)(v2c < 0.0f) << k;
-            if (m < m1) {
-              m2 = m1;
-              m1 = m;
-              am = k;
-            } else if (m < m2) {
-              m2 = m;
-            }
+            // sign bits collect from the top: after the loop bit (32 - len + k) holds position k.
+            // v2c is never -0 (every sum starts from +0 terms), so its sign bit equals v2c < 0.
+            sg = (sg >> 1) | (__float_as_uint(v2c) & 0x80000000u);
+            const bool lt = m < n1;
+            n2 = lt ? n1 : fminf(n2, m);
+            n1 = lt ? m : n1;
+            am = lt ? k : am;
           }
+          sg >>= (32 - len);
           const uint32_t par = ((uint32_t)__popc(sg) ^ (sv >> r)) & 1u;
-          st[0] = __float_as_uint(m1);
-          st[1] = __float_as_uint(m2);
-          st[2] = sg | ((uint32_t)am << 26) | (par << 31);
+          m1[r] = n1;
+          m2[r] = n2;
+          meta[r] = sg | ((uint32_t)am << 26) | (par << 31);
+          uint32_t nflip = sg ^ (0u - par);
           for (int k = 0; k < len; ++k) {
-            const int j = P.supp[r][k];
-            const float mag = (k == am) ? m2 : m1;
-            const float c = ((par ^ (sg >> k)) & 1u) ? -mag : mag;
-            U[own + j] = __fadd_rn(U[own + j], c);
+            const float mag = (k == am) ? n2 : n1;
+            const float c = __uint_as_float(__float_as_uint(mag) ^ (nflip << 31));
+            nflip >>= 1;
+            float* u = Us + P.supp[r][k] * TS + tid;
+            *u = __fadd_rn(*u, c);
           }
         }
       }
@@ -231,15 +241,19 @@ bp_kernel(BPArgs a, __grid_constant__ const SideParams P) {
   }
 }
 
-size_t bp_smem_bytes(const lead_code* code, int side, int spb) {
+size_t bp_smem_bytes(const lead_code* code, int side, int spb, int threads) {
   const SideParams& P = code->side[side].params;
-  return sizeof(uint32_t) * ((size_t)spb * P.order * code->nl * 2 + (size_t)spb * P.order * P.m_l * 3 +
-                             (size_t)spb * P.words_m + (size_t)spb * code->words_n + 2 * (size_t)spb);
+  return sizeof(uint32_t) * ((size_t)threads * code->nl * 3 + (size_t)spb * P.words_m +
+                             (size_t)spb * code->words_n + 2 * (size_t)spb);
 }
+
+}  // namespace
 
 int bp_shots_per_block(const lead_code* code) {
   return std::max(1, 256 / code->order);
 }
+
+namespace {
 
 size_t table_bytes(const lead_code* code, int side) {
   const size_t b = (size_t)(1 << code->side[side].m_l) * code->nl * sizeof(float);
@@ -296,7 +310,7 @@ int launch_local(const lead_code* code, const lead_decode_opts* o, const uint32_
   return LEAD_EINVAL;
 }
 
-template <int NL>
+template <int NL, int ML, int TS>
 int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* syn, int64_t shots,
               uint32_t* corr, uint8_t* status, int32_t* iters, float* llr, const float* table,
               cudaStream_t stream) {
@@ -316,20 +330,20 @@ int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* 
   a.iters = iters;
   a.llr = llr;
   a.table = table;
-  a.partner = code->dside[o->side].partner;
+  a.pa = code->dside[o->side].bp_pa;
   a.views = code->dside[o->side].views;
-  const size_t smem = bp_smem_bytes(code, o->side, a.spb);
+  if (a.spb * P.order != TS || P.m_l != ML || !a.pa) return LEAD_EINVAL;
+  const int threads = (TS + 31) / 32 * 32;
+  const size_t smem = bp_smem_bytes(code, o->side, a.spb, TS);
   if (smem > 227 * 1024) return LEAD_EINVAL;
-  const int threads = (a.spb * P.order + 31) / 32 * 32;
-  if (threads > kBPMaxThreads) return LEAD_EINVAL;
-  int rc = set_smem(bp_kernel<NL>, smem);
+  int rc = set_smem(bp_kernel<NL, ML, TS>, smem);
   if (rc != LEAD_OK) return rc;
   int per_sm = 0;
-  LEAD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bp_kernel<NL>, threads, smem));
+  LEAD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bp_kernel<NL, ML, TS>, threads, smem));
   if (per_sm < 1) return LEAD_EINVAL;
   const int64_t groups = (shots + a.spb - 1) / a.spb;
   const int64_t blocks = std::min<int64_t>(groups, (int64_t)sm_count(code->device) * per_sm);
-  bp_kernel<NL><<<(unsigned)blocks, threads, smem, stream>>>(a, P);
+  bp_kernel<NL, ML, TS><<<(unsigned)blocks, threads, smem, stream>>>(a, P);
   LEAD_CUDA_TRY(cudaGetLastError());
   return LEAD_OK;
 }
@@ -384,8 +398,13 @@ int lead_decode(const lead_code* code, const lead_decode_opts* opts, const uint3
     rc = launch_table(code, opts->side, opts->p, table, s);
     if (rc != LEAD_OK) return rc;
   }
-  if (code->nl == 16) return launch_bp<16>(code, opts, syn, shots, corr, status, iters, llr, table, s);
-  return launch_bp<36>(code, opts, syn, shots, corr, status, iters, llr, table, s);
+  const int ml = code->side[opts->side].m_l;
+  const int ts = bp_shots_per_block(code) * code->order;
+  if (code->nl == 16 && ml == 4 && ts == 240)      // |G| = 24 (SL(2,3)), 10 shots per CTA
+    return launch_bp<16, 4, 240>(code, opts, syn, shots, corr, status, iters, llr, table, s);
+  if (code->nl == 36 && ml == 9 && ts == 168)      // |G| = 168 (PSL(2,7)), 1 shot per CTA
+    return launch_bp<36, 9, 168>(code, opts, syn, shots, corr, status, iters, llr, table, s);
+  return LEAD_EINVAL;
 }
 
 }  // extern "C"

@@ -149,6 +149,25 @@ int prepare_side(lead_code* code, int s) {
   LEAD_TRY(upload(&ds.partner, hs.partner));
   LEAD_TRY(upload(&ds.qslots, hs.qslots));
   LEAD_TRY(upload(&ds.logicals, hs.logicals));
+  // min-sum kernel geometry: thread t = shot sl * order + vertex v of a CTA; slot (j, t) lives at
+  // shared-memory word j * ts + t; entry = address of the partner slot | this view first << 15
+  {
+    const int spb = bp_shots_per_block(code);
+    const int ts = spb * code->order;
+    if ((size_t)nl * ts < 32768) {
+      std::vector<uint16_t> pa((size_t)nl * ts, 0);
+      for (int sl = 0; sl < spb; ++sl)
+        for (int v = 0; v < code->order; ++v)
+          for (int j = 0; j < nl; ++j) {
+            const uint32_t raw = hs.partner[(size_t)v * nl + j];
+            const uint32_t ps = raw & 0x7FFFFFFFu;
+            const uint32_t vp = ps / nl, jp = ps % nl;
+            const int t = sl * code->order + v;
+            pa[(size_t)j * ts + t] = (uint16_t)((jp * ts + sl * code->order + vp) | ((raw >> 31) << 15));
+          }
+      LEAD_TRY(upload(&ds.bp_pa, pa));
+    }
+  }
   // syndrome contribution of row pattern x at row a: bit (rB*kRA + rA) = RA[rA][a] * (RB x)[rB]
   std::vector<uint16_t> contrib((size_t)delta << delta, 0);
   for (int a = 0; a < delta; ++a)
@@ -218,6 +237,7 @@ void release_device(lead_code* code) {
     cudaFree(ds.enumN1);
     cudaFree(ds.ml);
     cudaFree(ds.logicals);
+    cudaFree(ds.bp_pa);
     ds = DeviceSide{};
   }
   if (prev >= 0) cudaSetDevice(prev);

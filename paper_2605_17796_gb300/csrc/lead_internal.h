@@ -35,6 +35,7 @@ struct DeviceSide {
   int32_t* enumN1 = nullptr;     // 2^m_l x nl x (nl+1)
   uint64_t* ml = nullptr;        // 2^m_l least-weight coset members
   uint32_t* logicals = nullptr;  // k x words_n
+  uint16_t* bp_pa = nullptr;     // nl x (spb*order): partner shared-memory address | first << 15
 };
 
 struct HostSide {
@@ -69,4 +70,5 @@ namespace lead {
 // Implemented in the CUDA translation units.
 int prepare_device(lead_code* code, int device);
 void release_device(lead_code* code);
+int bp_shots_per_block(const lead_code* code);   // shots per CTA of the min-sum kernel
 }  // namespace lead
