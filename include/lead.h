@@ -219,6 +219,29 @@ int lead_decode(const lead_code* code, const lead_decode_opts* opts, const uint3
                 void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * lead_decode_noalloc -- lead_decode without a caller-provided workspace. The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate device memory: a
+ * real-time error-correction loop whose decode deadline leaves no room for cudaMalloc (which
+ * can block and synchronise the whole device), or an application whose own pool allocator owns
+ * all device memory. The local posterior table that lead_decode keeps in the workspace lives
+ * instead in one fixed device array of LEAD_NOALLOC_TABLE_BYTES bytes inside the library; every
+ * GPU that loads the library holds that array until the process exits.
+ *  Arguments and results are those of lead_decode. The call allocates nothing (no cudaMalloc,
+ *  no cudaFree, no allocating library routine).
+ *  The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *  that device current; make that first call before any stream capture.
+ *  All calls on a device share the array and it keeps the last call's table: calls whose device
+ *  work overlaps (other streams, or concurrent host threads) race on it and must be serialised
+ *  by the caller. Each call rewrites the whole table before reading it.
+ * Errors: those of lead_decode; LEAD_EINVAL also when the table (2^m_l * delta^2 floats) would
+ * exceed LEAD_NOALLOC_TABLE_BYTES.
+ */
+#define LEAD_NOALLOC_TABLE_BYTES 147456   /* 2^10 local syndromes x 36 floats */
+int lead_decode_noalloc(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn,
+                        int64_t shots, uint32_t* corr, uint8_t* status, int32_t* iters,
+                        float* llr, void* stream);
+
+/*
  * lead_check -- success test of Sec. IV-A on one side: residual r = err + corr.
  *  fail[shot] (dev uint8): bit 0 set iff H r != 0 (the correction misses the syndrome);
  *  bit 1 set iff H r = 0 and r is a nontrivial logical operator (it anticommutes with one of

@@ -408,3 +408,72 @@ int lead_decode(const lead_code* code, const lead_decode_opts* opts, const uint3
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Non-allocating decode. Some callers cannot allocate device memory for the workspace: a
+// quantum-error-correction control loop whose decode deadline leaves no room for cudaMalloc
+// (which may block and synchronise the device), or a host framework whose pool allocator owns
+// every byte of device memory. For them the local posterior table lives in a fixed file-scope
+// device array instead of the caller's workspace.
+// ---------------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace lead {
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+static_assert(LEAD_NOALLOC_TABLE_BYTES % 256 == 0, "table scratch must be a whole number of 256-byte blocks");
+
+// Shared by every call on a device and kept until the process exits; holds the last call's table.
+static __device__ __align__(256) float g_noalloc_table[LEAD_NOALLOC_TABLE_BYTES / sizeof(float)];
+
+std::mutex g_noalloc_mu;
+float* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Host-side address of the device array on the current device (set up once per device; the
+// array's name in host code is only a stand-in and must never be passed to a kernel).
+int noalloc_table(int device, float** out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return LEAD_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_table) != cudaSuccess || !p) return LEAD_ECUDA;
+    g_noalloc_addr[device] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_addr[device];
+  return LEAD_OK;
+}
+
+}  // namespace
+}  // namespace lead
+
+extern "C" int lead_decode_noalloc(const lead_code* code, const lead_decode_opts* opts,
+                                   const uint32_t* syn, int64_t shots, uint32_t* corr,
+                                   uint8_t* status, int32_t* iters, float* llr, void* stream) {
+  using namespace lead;
+  int rc = check_device(code);
+  if (rc != LEAD_OK) return rc;
+  rc = validate_opts(code, opts);
+  if (rc != LEAD_OK) return rc;
+  if (shots < 0) return LEAD_EINVAL;
+  if (opts->use_lead && table_bytes(code, opts->side) > (size_t)LEAD_NOALLOC_TABLE_BYTES) return LEAD_EINVAL;
+  float* table = nullptr;
+  if (opts->use_lead) {
+    rc = noalloc_table(code->device, &table);
+    if (rc != LEAD_OK) return rc;
+  }
+  if (shots == 0) return LEAD_OK;
+  if (!syn || !corr || !status) return LEAD_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (opts->use_lead) {
+    rc = launch_table(code, opts->side, opts->p, table, s);
+    if (rc != LEAD_OK) return rc;
+  }
+  const int ml = code->side[opts->side].m_l;
+  const int ts = bp_shots_per_block(code) * code->order;
+  if (code->nl == 16 && ml == 4 && ts == 240)
+    return launch_bp<16, 4, 240>(code, opts, syn, shots, corr, status, iters, llr, table, s);
+  if (code->nl == 36 && ml == 9 && ts == 168)
+    return launch_bp<36, 9, 168>(code, opts, syn, shots, corr, status, iters, llr, table, s);
+  return LEAD_EINVAL;
+}

@@ -63,6 +63,9 @@ EXPORTS = {
     "lead_decode": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_void_p,
                                    ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "lead_decode_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_void_p,
+                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
     "lead_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lead_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -218,6 +221,14 @@ class Code:
         nb = workspace.numel() * workspace.element_size() if workspace is not None else 0
         _check("lead_decode", LIB.lead_decode(self._h, ctypes.byref(opts), _ptr(syn), shots, _ptr(corr),
                                               _ptr(status), _ptr(iters), _ptr(llr), ws, nb, _stream(stream)))
+
+    def decode_noalloc(self, opts: LeadDecodeOpts, syn, shots: int, corr, status, iters=None, llr=None,
+                       stream=None):
+        """lead_decode_noalloc: like decode, with the library's fixed device scratch instead of a
+        caller workspace (for callers that cannot allocate device memory)."""
+        _check("lead_decode_noalloc", LIB.lead_decode_noalloc(self._h, ctypes.byref(opts), _ptr(syn), shots,
+                                                              _ptr(corr), _ptr(status), _ptr(iters), _ptr(llr),
+                                                              _stream(stream)))
 
     def check(self, side: int, err, corr, shots: int, fail, stream=None):
         _check("lead_check", LIB.lead_check(self._h, side, _ptr(err), _ptr(corr), shots, _ptr(fail),
