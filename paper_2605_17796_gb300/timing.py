@@ -1,0 +1,71 @@
+"""Time the library's kernels on one synthetic batch (CUDA events on the current stream).
+
+    python -m paper_2605_17796_gb300.timing --code PSL(2,7) --shots 65536 --p 0.05 --reps 3
+
+Samples X noise, then times lead_decode (LEAD or, with --baseline, plain min-sum) and
+lead_local_estimate on the same syndromes. Used for kernel tuning and for small ncu captures.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--code", default="PSL(2,7)")
+    ap.add_argument("--shots", type=int, default=65536)
+    ap.add_argument("--p", type=float, default=0.05)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--baseline", action="store_true")
+    ap.add_argument("--skip-local", action="store_true")
+    args = ap.parse_args(argv)
+
+    import torch
+    import workloads
+    from . import lead
+
+    inst = workloads.standard(args.code, 0)
+    code = lead.Code.from_instance(inst).prepare(0)
+    info = code.info
+    shots = args.shots
+    ex = torch.zeros((shots, info.words_n), dtype=torch.int32, device="cuda")
+    sz = torch.zeros((shots, info.words_m[0]), dtype=torch.int32, device="cuda")
+    code.sample(lead.NOISE_X, args.p, shots, 0, 0, err_x=ex, syn_z=sz)
+    o = lead.opts(side=0, p=args.p, use_lead=not args.baseline)
+    ws = torch.zeros(max(code.workspace_bytes(lead.opts(side=0, p=args.p)), 256) // 4 + 64,
+                     dtype=torch.int32, device="cuda")
+    corr = torch.zeros_like(ex)
+    st = torch.zeros(shots, dtype=torch.uint8, device="cuda")
+    it = torch.zeros(shots, dtype=torch.int32, device="cuda")
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.reps):
+        ms = timed(lambda: code.decode(o, sz, shots, corr, st, it, workspace=ws))
+        si = int(it.sum())
+        print(f"decode {args.code} {shots} shots p={args.p} {'baseline' if args.baseline else 'LEAD'}: "
+              f"{ms:.3f} ms, {shots / ms * 1e3:.3e} shots/s, {si} shot-iterations, "
+              f"{si / ms * 1e3:.3e} shot-iterations/s")
+    if not args.skip_local:
+        llr = torch.zeros((shots, info.n), dtype=torch.float32, device="cuda")
+        lo = lead.opts(side=0, p=args.p)
+        for _ in range(args.reps):
+            ms = timed(lambda: code.local_estimate(lo, sz, shots, llr, ws))
+            nbytes = shots * (info.n * 4 + info.words_m[0] * 4)
+            print(f"local_estimate {args.code} {shots} shots: {ms:.3f} ms, {shots / ms * 1e3:.3e} shots/s, "
+                  f"{nbytes / ms / 1e6:.1f} GB/s algorithmic")
+
+
+if __name__ == "__main__":
+    main()
