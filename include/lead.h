@@ -134,6 +134,17 @@ int lead_code_get_views(const lead_code* code, int32_t side, int32_t* views);
 int lead_code_get_check_matrix(const lead_code* code, int32_t side, uint8_t* H);
 
 /*
+ * lead_code_compile -- specialise the global min-sum kernel to this code (host only, no device
+ * needed): the kernel source is compiled at run time (NVRTC, sm_103a) with the code's local
+ * check supports as constants, so every loop over a check's support has a fixed trip count.
+ * lead_code_prepare calls it when it has not run yet; calling it first moves the compile time
+ * (about a second per side) out of the device set-up. log (host, nullable) receives the
+ * compiler log, truncated to log_bytes. Errors: LEAD_EINVAL (sizes the kernel cannot serve),
+ * LEAD_ECUDA (compilation failed; see the log).
+ */
+int lead_code_compile(lead_code* code, char* log, size_t log_bytes);
+
+/*
  * lead_code_prepare -- upload the code's tables to `device` and compute, on that device, the
  * exact local coset weight enumerators of both sides (the p-independent part of Phase 1:
  * N_s[w] = number of local patterns of weight w with local syndrome s, N1_s[j][w] those with

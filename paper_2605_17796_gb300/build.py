@@ -19,7 +19,10 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["device.cu", "sample.cu", "decode.cu"]
-CPP_SOURCES = ["code.cpp"]
+CPP_SOURCES = ["code.cpp", "jit.cpp"]
+# the run-time specialised min-sum kernel: these files are embedded (in this order) as text
+JIT_SOURCES = ["bp_jit_args.h", "lead_math.cuh", "bp_jit_kernel.cuh"]
+CUDA_HOME = "/usr/local/cuda"
 
 
 def _nvcc() -> str:
@@ -36,9 +39,27 @@ def _run(cmd):
     return r.stdout + r.stderr
 
 
+def _write_jit_source():
+    """Embed the specialised kernel's source as a C++ raw string (lead_jit_source.inc)."""
+    parts = []
+    for name in JIT_SOURCES:
+        text = open(os.path.join(CSRC, name)).read()
+        text = "\n".join(line for line in text.splitlines() if line.strip() != "#pragma once")
+        parts.append(f"// ---- {name}\n{text}\n")
+    body = "".join(parts)
+    if ")LEADJIT" in body:
+        raise RuntimeError("kernel source contains the raw-string delimiter")
+    out = os.path.join(BUILD, "lead_jit_source.inc")
+    new = 'static const char kLeadJitSource[] = R"LEADJIT(\n' + body + ')LEADJIT";\n'
+    if not os.path.exists(out) or open(out).read() != new:
+        with open(out, "w") as f:
+            f.write(new)
+
+
 def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     """Compile and link; returns the path of the shared library."""
     os.makedirs(BUILD, exist_ok=True)
+    _write_jit_source()
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", "-I", INCLUDE, "-Xcompiler", "-fPIC"]
     jobs = []
@@ -50,8 +71,8 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         jobs.append((cmd, obj))
     for src in CPP_SOURCES:
         obj = os.path.join(BUILD, src.replace(".cpp", ".o"))
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE,
-               "-I", "/usr/local/cuda/include", "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", BUILD,
+               "-I", os.path.join(CUDA_HOME, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
         jobs.append((cmd, obj))
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         outs = list(ex.map(lambda j: _run(j[0]), jobs))
@@ -60,7 +81,9 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
             if o.strip():
                 print(o)
     tmp = LIB + ".tmp"
-    _run([nvcc, *ARCH, "-shared", "-o", tmp, *[o for _, o in jobs]])
+    libdir = os.path.join(CUDA_HOME, "lib64")
+    _run([nvcc, *ARCH, "-shared", "-o", tmp, *[o for _, o in jobs], "-L", libdir,
+          "-lnvrtc", "-Xlinker", f"-rpath,{libdir}"])
     os.replace(tmp, LIB)
     return LIB
 

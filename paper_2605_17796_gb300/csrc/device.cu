@@ -212,14 +212,22 @@ int prepare_side(lead_code* code, int s) {
 int prepare_device(lead_code* code, int device) {
   if (code->device == device) return LEAD_OK;
   if (code->device >= 0) return LEAD_ESTATE;
+  int rc = jit_compile(code, nullptr);       // host-only; skipped if lead_code_compile ran
+  if (rc != LEAD_OK) return rc;
   LEAD_CUDA_TRY(cudaSetDevice(device));
+  LEAD_CUDA_TRY(cudaFree(nullptr));           // make the device's primary context current
   code->device = device;
   for (int s = 0; s < 2; ++s) {
-    int rc = prepare_side(code, s);
+    rc = prepare_side(code, s);
     if (rc != LEAD_OK) {
       release_device(code);
       return rc;
     }
+  }
+  rc = jit_load(code);
+  if (rc != LEAD_OK) {
+    release_device(code);
+    return rc;
   }
   return LEAD_OK;
 }
@@ -229,6 +237,7 @@ void release_device(lead_code* code) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(code->device);
+  jit_unload(code);
   for (auto& ds : code->dside) {
     cudaFree(ds.views);
     cudaFree(ds.partner);

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "../../include/lead.h"
@@ -36,6 +37,9 @@ struct DeviceSide {
   uint64_t* ml = nullptr;        // 2^m_l least-weight coset members
   uint32_t* logicals = nullptr;  // k x words_n
   uint16_t* bp_pa = nullptr;     // nl x (spb*order): partner shared-memory address | first << 15
+  void* bp_module = nullptr;     // cudaLibrary_t of the specialised min-sum kernel
+  void* bp_func = nullptr;       // its cudaKernel_t
+  int bp_per_sm = 0;             // resident CTAs per SM
 };
 
 struct HostSide {
@@ -51,6 +55,9 @@ struct HostSide {
   std::vector<uint8_t> RA, RB;       // row factors: local checks = kron(RB, RA)
   int32_t kRA = 0, kRB = 0;
   SideParams params{};
+  std::vector<char> bp_cubin;        // specialised min-sum kernel (NVRTC output)
+  int bp_block = 0, bp_spb = 0;
+  size_t bp_smem = 0;
 };
 
 }  // namespace lead
@@ -71,4 +78,9 @@ namespace lead {
 int prepare_device(lead_code* code, int device);
 void release_device(lead_code* code);
 int bp_shots_per_block(const lead_code* code);   // shots per CTA of the min-sum kernel
+struct BPJitArgs;
+int jit_compile(lead_code* code, std::string* log);
+int jit_load(lead_code* code);
+void jit_unload(lead_code* code);
+int jit_launch_bp(const lead_code* code, int side, const BPJitArgs& args, int sm_count, void* stream);
 }  // namespace lead

@@ -47,6 +47,7 @@ EXPORTS = {
     "lead_code_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadCodeInfo)]),
     "lead_code_get_views": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _c_int32_p]),
     "lead_code_get_check_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _c_uint8_p]),
+    "lead_code_compile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "lead_code_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "lead_code_get_enumerators": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _c_int32_p, _c_int32_p,
                                                  ctypes.POINTER(ctypes.c_uint64)]),
@@ -178,6 +179,14 @@ class Code:
         _check("lead_code_get_check_matrix",
                LIB.lead_code_get_check_matrix(self._h, side, out.ctypes.data_as(_c_uint8_p)))
         return out
+
+    def compile(self) -> str:
+        """Specialise the min-sum kernel to this code (host only); returns the compiler log."""
+        buf = ctypes.create_string_buffer(1 << 16)
+        rc = LIB.lead_code_compile(self._h, buf, len(buf))
+        if rc != 0:
+            raise LeadError("lead_code_compile", rc) from RuntimeError(buf.value.decode(errors="replace"))
+        return buf.value.decode(errors="replace")
 
     def prepare(self, device: int = 0) -> "Code":
         _check("lead_code_prepare", LIB.lead_code_prepare(self._h, device))

@@ -83,3 +83,12 @@ def test_device_calls_refuse_unprepared_code(lead):
     code = lead.Code.from_instance(inst)
     rc = lead.LIB.lead_check(code._h, 0, None, None, 0, None, None)
     assert rc == -8          # LEAD_ESTATE: no device tables
+
+
+@pytest.mark.parametrize("name", ["SL(2,3)", "PSL(2,7)"])
+def test_min_sum_kernel_specialises_without_a_gpu(lead, name):
+    """lead_code_compile runs NVRTC for sm_103a on the host; no device is needed."""
+    code = lead.Code.from_instance(workloads.standard(name, 0))
+    log = code.compile()
+    assert "error" not in log.lower()
+    code.compile()        # a second call is a no-op
