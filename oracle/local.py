@@ -284,49 +284,74 @@ def macwilliams_zero_coset(L: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------------------
 # Single-precision decision path. Floating point decides the hard decisions of the global
 # decoder, so the oracle evaluates the prior LLR that feeds it in IEEE binary32 with a fixed
-# operation order: boost and merge in binary32, and the natural logarithm by the inverse
-# hyperbolic tangent series ln m = 2 atanh z, z = (m-1)/(m+1) (Abramowitz & Stegun 4.1.27),
-# on m in [sqrt(1/2), sqrt(2)) after extracting the binary exponent. Coefficients are the
-# nearest binary32 values of 2/k; ln 2 and sqrt 2 likewise.
+# operation order, exactly as a single-precision implementation must:
+#   * boost and merge in binary32, p clamped to [2^-23, 1 - 2^-23];
+#   * lambda(p) = ln((1 - p)/p) by linear interpolation in a table over p in [2^-23, 1/2]:
+#     node i is the binary32 number with bit pattern (i + 13312) << 16 (the exponent and the
+#     top 7 fraction bits of p), T0[i] = lambda at node i, T1[i] = slope to node i + 1, and
+#     lambda = T0[i] + (p - p_i) * T1[i] (p - p_i is exact); for p > 1/2, lambda(p) = -lambda(1-p)
+#     (1 - p is exact there). Interpolation error <= (p/128)^2 / (8 p^2) ~ 7.6e-6.
+#   * the table entries are computed in binary64 from a logarithm evaluated by the inverse
+#     hyperbolic tangent series ln m = 2 atanh((m-1)/(m+1)) (Abramowitz & Stegun 4.1.27) with
+#     explicit operations, then rounded to binary32, so any implementation following the same
+#     steps obtains the same table bit for bit.
 # ---------------------------------------------------------------------------------------
 
-def _f32(bits: int) -> np.float32:
-    return np.array([bits], dtype=np.uint32).view(np.float32)[0]
-
-
-LN2_F = _f32(0x3F317218)
-SQRT2_F = _f32(0x3FB504F3)
-SERIES_F = [_f32(0x40000000), _f32(0x3F2AAAAB), _f32(0x3ECCCCCD), _f32(0x3E924925),
-            _f32(0x3E638E39), _f32(0x3E3A2E8C)]          # 2/1, 2/3, 2/5, 2/7, 2/9, 2/11
+LN2_D = np.array([0x3FE62E42FEFA39EF], dtype=np.uint64).view(np.float64)[0]     # nearest double to ln 2
+SQRT2_D = np.array([0x3FF6A09E667F3BCD], dtype=np.uint64).view(np.float64)[0]   # nearest double to sqrt 2
 P_MIN_F = np.float32(2.0 ** -23)
 P_MAX_F = np.float32(1.0 - 2.0 ** -23)
+LLR_NODE0 = 13312                   # (2^-23 bit pattern) >> 16
+LLR_NODES = 2817                    # nodes 2^-23 ... 1/2
 
 
-def log_f32(x: np.ndarray) -> np.ndarray:
-    """Natural log of positive normal binary32 values, evaluated in binary32 as described above."""
-    x = np.asarray(x, dtype=np.float32)
-    bits = x.view(np.uint32)
-    e = ((bits >> np.uint32(23)) & np.uint32(0xFF)).astype(np.int32) - 127
-    m = ((bits & np.uint32(0x7FFFFF)) | np.uint32(0x3F800000)).view(np.float32)
-    big = m > SQRT2_F
-    m = np.where(big, m * np.float32(0.5), m).astype(np.float32)
-    e = e + big.astype(np.int32)
-    z = ((m - np.float32(1.0)) / (m + np.float32(1.0))).astype(np.float32)
-    w = (z * z).astype(np.float32)
-    s = np.full(x.shape, SERIES_F[5], dtype=np.float32)
-    for c in (SERIES_F[4], SERIES_F[3], SERIES_F[2], SERIES_F[1], SERIES_F[0]):
-        s = (s * w).astype(np.float32)
-        s = (s + c).astype(np.float32)
-    a = (e.astype(np.float32) * LN2_F).astype(np.float32)
-    b = (z * s).astype(np.float32)
-    return (a + b).astype(np.float32)
+def log_series_f64(x: np.ndarray) -> np.ndarray:
+    """ln x for positive normal binary64 x: x = 2^e m, m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh z
+    with z = (m - 1)/(m + 1), series through z^25 (error below 1e-16 for |z| <= 0.1716)."""
+    x = np.asarray(x, dtype=np.float64)
+    bits = x.view(np.uint64)
+    e = ((bits >> np.uint64(52)) & np.uint64(0x7FF)).astype(np.int64) - 1023
+    m = ((bits & np.uint64(0x000FFFFFFFFFFFFF)) | np.uint64(0x3FF0000000000000)).view(np.float64)
+    big = m > SQRT2_D
+    m = np.where(big, m * 0.5, m)
+    e = e + big.astype(np.int64)
+    z = (m - 1.0) / (m + 1.0)
+    w = z * z
+    s = np.full(x.shape, 2.0 / 25.0)
+    for k in range(23, 0, -2):
+        s = s * w
+        s = s + 2.0 / k
+    return e.astype(np.float64) * LN2_D + z * s
+
+
+def llr_tables():
+    """(T0, T1) binary32 node values and slopes of lambda(p) = ln((1 - p)/p) on [2^-23, 1/2]."""
+    i = np.arange(LLR_NODES + 1, dtype=np.uint32)
+    pn = ((i + np.uint32(LLR_NODE0)) << np.uint32(16)).view(np.float32).astype(np.float64)
+    lam = log_series_f64(1.0 - pn) - log_series_f64(pn)
+    T0 = lam[:LLR_NODES].astype(np.float32)
+    T1 = ((lam[1:] - lam[:-1]) / (pn[1:] - pn[:-1])).astype(np.float32)
+    T1[LLR_NODES - 1] = np.float32(0.0)            # the node p = 1/2 is only used with p - p_i = 0
+    return T0, T1
+
+
+_LLR_T = None
 
 
 def llr_f32(p: np.ndarray) -> np.ndarray:
-    """lambda = ln((1 - p)/p) in binary32 after clamping p to [2^-23, 1 - 2^-23]."""
+    """lambda = ln((1 - p)/p) on the binary32 decision track (see the block comment above)."""
+    global _LLR_T
+    if _LLR_T is None:
+        _LLR_T = llr_tables()
+    T0, T1 = _LLR_T
     p = np.clip(np.asarray(p, dtype=np.float32), P_MIN_F, P_MAX_F).astype(np.float32)
-    x = ((np.float32(1.0) - p) / p).astype(np.float32)
-    return log_f32(x)
+    hi = p > np.float32(0.5)
+    q = np.where(hi, (np.float32(1.0) - p).astype(np.float32), p).astype(np.float32)
+    idx = (q.view(np.uint32) >> np.uint32(16)).astype(np.int64) - LLR_NODE0
+    node = ((idx + LLR_NODE0).astype(np.uint32) << np.uint32(16)).view(np.float32)
+    d = (q - node).astype(np.float32)
+    lam = (T0[idx] + (d * T1[idx]).astype(np.float32)).astype(np.float32)
+    return np.where(hi, -lam, lam).astype(np.float32)
 
 
 def boosted_table_f32(N, N1, ml_mask, p: float) -> np.ndarray:

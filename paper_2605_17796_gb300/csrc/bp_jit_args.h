@@ -23,6 +23,8 @@ struct BPJitArgs {
   const float* table;           // 2^m_l x nl local posterior table (nullptr for the baseline)
   const unsigned short* pa;     // [j][t] partner shared-memory address | first view << 15
   const unsigned short* views;  // [v][j] qubit index
+  const float* llr_t0;          // prior-LLR interpolation table: node values
+  const float* llr_t1;          //   and slopes
 };
 
 }  // namespace lead

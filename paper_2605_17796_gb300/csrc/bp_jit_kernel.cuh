@@ -40,7 +40,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
   const int tid = threadIdx.x;
   const int sl = tid / V, v = tid - sl * V;
   const bool lane_ok = tid < TS;
-  const float lam_ch = a.use_lead ? 0.0f : lead::channel_llr(a.p);
+  const float lam_ch = a.use_lead ? 0.0f : lead::channel_llr(a.p, a.llr_t0, a.llr_t1);
 
   for (long long g0 = (long long)blockIdx.x * spb; g0 < a.shots; g0 += (long long)gridDim.x * spb) {
     const int nsh = (int)((a.shots - g0) < spb ? (a.shots - g0) : spb);
@@ -67,7 +67,8 @@ lead_bp_jit(const lead::BPJitArgs a) {
           const unsigned int addr = __ldg(PA + j * TS + tid) & 0x7FFFu;
           const unsigned int jp = addr / TS, vp = addr - jp * TS - sl * V;
           const unsigned int svp = lead::bit_field(srow, vp * ML, ML);
-          Ls[j * TS + tid] = lead::merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp), a.alpha);
+          Ls[j * TS + tid] = lead::merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp),
+                                              a.alpha, a.llr_t0, a.llr_t1);
         } else {
           Ls[j * TS + tid] = lam_ch;
         }

@@ -13,56 +13,67 @@ int launch_table(const lead_code* code, int side, double p, float* table, cudaSt
 
 namespace {
 
-constexpr int kLocalThreads = 256;
-constexpr int kLocalShotBatch = 8;
+constexpr int kLocalThreads = 512;
+constexpr int kLocalShotBatch = 32;
 
 struct LocalArgs {
-  int32_t n, spb_rows;
+  int32_t n, order;
   float alpha;
   int64_t shots;
   const uint32_t* syn;
   const float* table;
   const uint32_t* qslots;
+  const float* llr_t0;
+  const float* llr_t1;
   float* llr;
 };
 
-// Phases 1-2 for every (shot, qubit): the two views' boosted local posteriors are read from the
-// per-syndrome table (held in shared memory) and merged into the prior LLR. Each thread keeps
-// the view slots of its qubits in registers across all shots of the persistent loop.
+// Phases 1-2 for every (shot, qubit): per batch of shots, the local syndromes s_v of all
+// vertices are extracted once into shared memory; then every qubit reads its two views'
+// boosted local posteriors from the per-syndrome table (shared memory) and merges them into
+// the prior LLR. Each thread keeps its qubits' view coordinates in registers for the whole
+// persistent loop; the LLR rows are written with consecutive threads on consecutive qubits.
 template <int NL, int KQ>
-__global__ void __launch_bounds__(kLocalThreads)
+__global__ void __launch_bounds__(kLocalThreads, 2)
 local_estimate_kernel(LocalArgs a, __grid_constant__ const SideParams P) {
   extern __shared__ __align__(16) uint32_t smem[];
   float* tab = reinterpret_cast<float*>(smem);
   const int tab_n = (1 << P.m_l) * NL;
-  uint32_t* syn_s = smem + tab_n;
+  // prior-LLR interpolation table staged once as (node value, slope) pairs: one 8-byte load
+  float2* tv = reinterpret_cast<float2*>(tab + tab_n + (tab_n & 1));
+  uint16_t* sv_s = reinterpret_cast<uint16_t*>(tv + kLlrNodes);   // [batch shot][vertex]
   for (int i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = __ldg(a.table + i);
-  uint32_t s0[KQ], s1[KQ];
+  for (int i = threadIdx.x; i < kLlrNodes; i += blockDim.x) tv[i] = make_float2(__ldg(a.llr_t0 + i), __ldg(a.llr_t1 + i));
+  uint32_t vv[KQ], jj[KQ];       // (v0 | v1 << 16), (j0 | j1 << 16)
 #pragma unroll
   for (int k = 0; k < KQ; ++k) {
     const int i = threadIdx.x + k * kLocalThreads;
-    s0[k] = i < a.n ? __ldg(a.qslots + 2 * i) : 0u;
-    s1[k] = i < a.n ? __ldg(a.qslots + 2 * i + 1) : 0u;
+    const uint32_t s0 = i < a.n ? __ldg(a.qslots + 2 * i) : 0u;
+    const uint32_t s1 = i < a.n ? __ldg(a.qslots + 2 * i + 1) : 0u;
+    vv[k] = (s0 / NL) | ((s1 / NL) << 16);
+    jj[k] = (s0 % NL) | ((s1 % NL) << 16);
   }
-  const int wm = P.words_m;
+  const int wm = P.words_m, V = a.order, ml = P.m_l;
   for (int64_t b0 = (int64_t)blockIdx.x * kLocalShotBatch; b0 < a.shots;
        b0 += (int64_t)gridDim.x * kLocalShotBatch) {
-    const int nsh = (int)rows_left(kLocalShotBatch, a.shots - b0);
+    const int nsh = rows_left(kLocalShotBatch, a.shots - b0);
     __syncthreads();
-    for (int i = threadIdx.x; i < nsh * wm; i += blockDim.x) syn_s[i] = __ldg(a.syn + b0 * wm + i);
+    for (int i = threadIdx.x; i < nsh * V; i += blockDim.x) {
+      const int sl = i / V, v = i - sl * V;
+      sv_s[i] = (uint16_t)bit_field(a.syn + (b0 + sl) * wm, v * ml, ml);
+    }
     __syncthreads();
+#pragma unroll 4
     for (int sl = 0; sl < nsh; ++sl) {
-      const uint32_t* row = syn_s + sl * wm;
+      const uint16_t* svr = sv_s + sl * V;
       float* out = a.llr + (b0 + sl) * (int64_t)a.n;
 #pragma unroll
       for (int k = 0; k < KQ; ++k) {
         const int i = threadIdx.x + k * kLocalThreads;
         if (i < a.n) {
-          const uint32_t v0 = s0[k] / NL, j0 = s0[k] - v0 * NL;
-          const uint32_t v1 = s1[k] / NL, j1 = s1[k] - v1 * NL;
-          const uint32_t q0 = bit_field(row, v0 * P.m_l, P.m_l);
-          const uint32_t q1 = bit_field(row, v1 * P.m_l, P.m_l);
-          out[i] = merged_llr(tab[q0 * NL + j0], tab[q1 * NL + j1], a.alpha);
+          const float q0 = tab[svr[vv[k] & 0xFFFFu] * NL + (jj[k] & 0xFFFFu)];
+          const float q1 = tab[svr[vv[k] >> 16] * NL + (jj[k] >> 16)];
+          __stcs(out + i, merged_llr_s(q0, q1, a.alpha, tv));
         }
       }
     }
@@ -105,13 +116,17 @@ int launch_local(const lead_code* code, const lead_decode_opts* o, const uint32_
   const SideParams& P = code->side[o->side].params;
   LocalArgs a{};
   a.n = code->n;
+  a.order = code->order;
   a.alpha = o->alpha;
   a.shots = shots;
   a.syn = syn;
   a.table = table;
   a.qslots = code->dside[o->side].qslots;
+  a.llr_t0 = code->d_llr;
+  a.llr_t1 = code->d_llr + kLlrNodes;
   a.llr = llr;
-  const size_t smem = sizeof(uint32_t) * ((size_t)(1 << P.m_l) * NL + (size_t)kLocalShotBatch * P.words_m);
+  const size_t smem = sizeof(uint32_t) * ((size_t)(1 << P.m_l) * NL + 1 + 2 * (size_t)kLlrNodes) +
+                      sizeof(uint16_t) * (size_t)kLocalShotBatch * code->order;
   const int kq = (code->n + kLocalThreads - 1) / kLocalThreads;
   auto pick = [&](auto kern) -> int {
     int rc = set_smem(kern, smem);
@@ -125,10 +140,10 @@ int launch_local(const lead_code* code, const lead_decode_opts* o, const uint32_
     LEAD_CUDA_TRY(cudaGetLastError());
     return LEAD_OK;
   };
+  if (kq <= 1) return pick(local_estimate_kernel<NL, 1>);
   if (kq <= 2) return pick(local_estimate_kernel<NL, 2>);
-  if (kq <= 4) return pick(local_estimate_kernel<NL, 4>);
-  if (kq <= 12) return pick(local_estimate_kernel<NL, 12>);
-  if (kq <= 48) return pick(local_estimate_kernel<NL, 48>);
+  if (kq <= 6) return pick(local_estimate_kernel<NL, 6>);
+  if (kq <= 24) return pick(local_estimate_kernel<NL, 24>);
   return LEAD_EINVAL;
 }
 
@@ -154,6 +169,8 @@ int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* 
   a.table = table;
   a.pa = code->dside[o->side].bp_pa;
   a.views = code->dside[o->side].views;
+  a.llr_t0 = code->d_llr;
+  a.llr_t1 = code->d_llr + kLlrNodes;
   if (!a.pa) return LEAD_EINVAL;
   return jit_launch_bp(code, o->side, a, sm_count(code->device), stream);
 }

@@ -123,6 +123,19 @@ __global__ void table_kernel(int nl, int m_l, double r, const int32_t* __restric
   }
 }
 
+// Nodes and slopes of lambda(p) = ln((1 - p)/p) on [2^-23, 1/2] (see llr_interp), from the
+// binary64 logarithm series, rounded to binary32.
+__global__ void llr_table_kernel(float* __restrict__ t0, float* __restrict__ t1) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kLlrNodes; i += gridDim.x * blockDim.x) {
+    const double p0 = (double)__uint_as_float((unsigned)(i + kLlrNode0) << 16);
+    const double p1 = (double)__uint_as_float((unsigned)(i + 1 + kLlrNode0) << 16);
+    const double l0 = __dsub_rn(log_series_f64(__dsub_rn(1.0, p0)), log_series_f64(p0));
+    const double l1 = __dsub_rn(log_series_f64(__dsub_rn(1.0, p1)), log_series_f64(p1));
+    t0[i] = __double2float_rn(l0);
+    t1[i] = (i == kLlrNodes - 1) ? 0.0f : __double2float_rn(__ddiv_rn(__dsub_rn(l1, l0), __dsub_rn(p1, p0)));
+  }
+}
+
 template <typename T>
 int upload(T** dst, const std::vector<T>& src) {
   if (src.empty()) {
@@ -224,6 +237,15 @@ int prepare_device(lead_code* code, int device) {
       return rc;
     }
   }
+  if (cudaMalloc(&code->d_llr, 2 * kLlrNodes * sizeof(float)) != cudaSuccess) {
+    release_device(code);
+    return LEAD_EOOM;
+  }
+  llr_table_kernel<<<(kLlrNodes + 255) / 256, 256>>>(code->d_llr, code->d_llr + kLlrNodes);
+  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    release_device(code);
+    return LEAD_ECUDA;
+  }
   rc = jit_load(code);
   if (rc != LEAD_OK) {
     release_device(code);
@@ -249,6 +271,8 @@ void release_device(lead_code* code) {
     cudaFree(ds.bp_pa);
     ds = DeviceSide{};
   }
+  cudaFree(code->d_llr);
+  code->d_llr = nullptr;
   if (prev >= 0) cudaSetDevice(prev);
   code->device = -1;
 }

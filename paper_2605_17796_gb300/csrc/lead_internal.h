@@ -71,6 +71,7 @@ struct lead_code {
   lead::HostSide side[2];
   int32_t device = -1;
   lead::DeviceSide dside[2];
+  float* d_llr = nullptr;            // prior-LLR interpolation table: node values, then slopes
 };
 
 namespace lead {

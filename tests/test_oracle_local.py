@@ -150,22 +150,34 @@ def test_posterior_fourier_form_fp64(psl7):
             assert abs((1 - Tj / T) / 2 - q[s, j]) < 1e-12
 
 
-def test_log_f32_accuracy():
+def test_log_series_f64_accuracy():
     rng = np.random.default_rng(0)
-    x = np.concatenate([np.exp(rng.uniform(-16.5, 16.5, 200000)), [1.0, 2.0, 0.5, 1.4142135, 1.4142137]])
-    x = x.astype(np.float32)
-    got = local.log_f32(x).astype(np.float64)
-    ref = np.log(x.astype(np.float64))
-    assert np.abs(got - ref).max() < 4e-6
-    assert np.abs((got - ref) / np.maximum(np.abs(ref), 1e-3)).max() < 1e-5
+    x = np.concatenate([np.exp(rng.uniform(-40, 40, 100000)), [1.0, 2.0, 0.5, np.sqrt(2.0)]])
+    got = local.log_series_f64(x)
+    ref = np.log(x)
+    assert np.abs(got - ref).max() <= 4e-15 * np.maximum(1.0, np.abs(ref)).max()
 
 
 def test_llr_f32_matches_fp64():
-    p = np.linspace(1e-6, 1 - 1e-6, 100001)
-    got = local.llr_f32(p.astype(np.float32)).astype(np.float64)
-    p32 = p.astype(np.float32).astype(np.float64)
-    ref = np.log((1 - p32) / p32)
-    assert np.abs(got - ref).max() < 1e-5
+    """The interpolated binary32 LLR stays within 2e-5 of ln((1-p)/p) on the whole clamp range,
+    and within its interpolation bound (p/128)^2 / (8 p^2) + rounding."""
+    p = np.concatenate([np.geomspace(2.0 ** -23, 0.5, 200001), np.linspace(0.5, 1 - 2.0 ** -23, 100001)])
+    p32 = p.astype(np.float32)
+    got = local.llr_f32(p32).astype(np.float64)
+    q = np.clip(p32.astype(np.float64), 2.0 ** -23, 1 - 2.0 ** -23)
+    ref = np.log((1 - q) / q)
+    assert np.abs(got - ref).max() < 2e-5
+    # lambda(p) = -lambda(1 - p) exactly for p > 1/2, where 1 - p is exact in binary32
+    s = np.linspace(0.5, 1 - 2.0 ** -23, 1001)[1:].astype(np.float32)
+    assert (local.llr_f32(s) == -local.llr_f32((np.float32(1) - s).astype(np.float32))).all()
+
+
+def test_llr_nodes_hit_exactly():
+    T0, T1 = local.llr_tables()
+    i = np.arange(local.LLR_NODES, dtype=np.uint32)
+    nodes = ((i + np.uint32(local.LLR_NODE0)) << np.uint32(16)).view(np.float32)
+    assert (local.llr_f32(nodes) == T0).all()
+    assert T0[-1] == 0.0                       # lambda(1/2) = 0
 
 
 def test_boost_applies_to_ml_bits(psl7):
