@@ -162,23 +162,37 @@ int prepare_side(lead_code* code, int s) {
   LEAD_TRY(upload(&ds.partner, hs.partner));
   LEAD_TRY(upload(&ds.qslots, hs.qslots));
   LEAD_TRY(upload(&ds.logicals, hs.logicals));
-  // min-sum kernel geometry: thread t = shot sl * order + vertex v of a CTA; slot (j, t) lives at
-  // shared-memory word j * ts + t; entry = address of the partner slot | this view first << 15
+  // min-sum kernel partner table. One CTA per shot group: thread t = shot sl * order + vertex v,
+  // slot (j, t) lives at shared-memory word j * ts + t; entry = partner address | first << 15.
+  // Cluster launch: CTA rank r owns vertices r*ts .. r*ts + ts - 1; entry (u32, indexed [j][v]) =
+  // partner word address inside its owner | owner rank << 16 | first << 31.
   {
-    const int spb = bp_shots_per_block(code);
-    const int ts = spb * code->order;
-    if ((size_t)nl * ts < 32768) {
-      std::vector<uint16_t> pa((size_t)nl * ts, 0);
-      for (int sl = 0; sl < spb; ++sl)
+    const Geometry g = bp_geometry(code, s);
+    if (g.cluster == 1 && (size_t)nl * g.ts < 32768) {
+      std::vector<uint16_t> pa((size_t)nl * g.ts, 0);
+      for (int sl = 0; sl < g.spb; ++sl)
         for (int v = 0; v < code->order; ++v)
           for (int j = 0; j < nl; ++j) {
             const uint32_t raw = hs.partner[(size_t)v * nl + j];
             const uint32_t ps = raw & 0x7FFFFFFFu;
             const uint32_t vp = ps / nl, jp = ps % nl;
             const int t = sl * code->order + v;
-            pa[(size_t)j * ts + t] = (uint16_t)((jp * ts + sl * code->order + vp) | ((raw >> 31) << 15));
+            pa[(size_t)j * g.ts + t] = (uint16_t)((jp * g.ts + sl * code->order + vp) | ((raw >> 31) << 15));
           }
       LEAD_TRY(upload(&ds.bp_pa, pa));
+    } else if (g.cluster > 1) {
+      std::vector<uint32_t> pa((size_t)nl * code->order, 0);
+      for (int v = 0; v < code->order; ++v)
+        for (int j = 0; j < nl; ++j) {
+          const uint32_t raw = hs.partner[(size_t)v * nl + j];
+          const uint32_t ps = raw & 0x7FFFFFFFu;
+          const uint32_t vp = ps / nl, jp = ps % nl;
+          const uint32_t owner = vp / g.ts, tp = vp - owner * g.ts;
+          pa[(size_t)j * code->order + v] = (jp * g.ts + tp) | (owner << 16) | (raw & 0x80000000u);
+        }
+      uint32_t* d = nullptr;
+      LEAD_TRY(upload(&d, pa));
+      ds.bp_pa = reinterpret_cast<uint16_t*>(d);
     }
   }
   // syndrome contribution of row pattern x at row a: bit (rB*kRA + rA) = RA[rA][a] * (RB x)[rB]

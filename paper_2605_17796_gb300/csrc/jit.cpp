@@ -23,19 +23,28 @@ namespace lead {
 
 namespace {
 
-struct Geometry {
-  int spb, ts, block, minblocks;
-  size_t smem;
-};
+}  // namespace
 
-Geometry geometry(const lead_code* code, int side) {
+Geometry bp_geometry(const lead_code* code, int side) {
   const SideParams& P = code->side[side].params;
   Geometry g{};
+  auto smem_for = [&](int ts, int spb) {
+    return sizeof(uint32_t) * ((size_t)ts * code->nl * 3 + (size_t)spb * P.words_m + (size_t)spb * code->words_n +
+                               2 * (size_t)spb);
+  };
   g.spb = bp_shots_per_block(code);
+  g.cluster = 1;
   g.ts = g.spb * code->order;
+  g.smem = smem_for(g.ts, g.spb);
+  // a shot whose state does not leave room for two CTAs per SM is split over a thread-block
+  // cluster (distributed shared memory), 2, 4 or 8 CTAs
+  while (g.smem > 120u * 1024u && g.cluster < 8) {
+    g.cluster *= 2;
+    g.spb = 1;
+    g.ts = (code->order + g.cluster - 1) / g.cluster;
+    g.smem = smem_for(g.ts, 1);
+  }
   g.block = (g.ts + 31) / 32 * 32;
-  g.smem = sizeof(uint32_t) * ((size_t)g.ts * code->nl * 3 + (size_t)g.spb * P.words_m +
-                               (size_t)g.spb * code->words_n + 2 * (size_t)g.spb);
   // CTAs per SM that shared memory allows (227 KB usable, 1 KB reserved per CTA), capped so
   // that each thread keeps at least 64 registers
   int by_smem = (int)((227u * 1024u) / (g.smem + 1024));
@@ -43,6 +52,8 @@ Geometry geometry(const lead_code* code, int side) {
   g.minblocks = std::max(1, std::min(by_smem, by_regs));
   return g;
 }
+
+namespace {
 
 std::string prelude(const lead_code* code, int side, const Geometry& g) {
   const SideParams& P = code->side[side].params;
@@ -56,6 +67,7 @@ std::string prelude(const lead_code* code, int side, const Geometry& g) {
     << "#define LEAD_MINBLOCKS " << g.minblocks << "\n"
     << "#define LEAD_KMAX " << kmax << "\n"
     << "#define LEAD_SPB " << g.spb << "\n"
+    << "#define LEAD_CLUSTER " << g.cluster << "\n"
     << "namespace lead_jit {\n";
   s << "__device__ constexpr int kLen[" << P.m_l << "] = {";
   for (int r = 0; r < P.m_l; ++r) s << (r ? "," : "") << P.supp_len[r];
@@ -93,23 +105,33 @@ int jit_compile(lead_code* code, std::string* log_out) {
   for (int side = 0; side < 2; ++side) {
     HostSide& hs = code->side[side];
     if (!hs.bp_cubin.empty()) continue;
-    const Geometry g = geometry(code, side);
-    if (g.block > 1024 || (size_t)code->nl * g.ts >= 32768) return LEAD_EINVAL;
+    const Geometry g = bp_geometry(code, side);
+    if (g.block > 1024 || (size_t)code->nl * g.ts >= 32768 || g.smem > 227u * 1024u) return LEAD_EINVAL;
     const std::string src = prelude(code, side, g) + kLeadJitSource;
     nvrtcProgram prog;
     if (nvrtcCreateProgram(&prog, src.c_str(), "lead_bp_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
       return LEAD_ECUDA;
     // LEAD_JIT_PTXAS_VERBOSE=1 adds the assembler's register / spill report to the log
     const char* verbose = std::getenv("LEAD_JIT_PTXAS_VERBOSE");
+    // registers per thread that let LEAD_MINBLOCKS CTAs of this size share an SM
+    const int maxreg = std::min(255, (65536 / (g.block * g.minblocks)) & ~7);
+    const std::string regopt = "--maxrregcount=" + std::to_string(maxreg);
     const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=false", "-lineinfo",
-                          "--ptxas-options=-v"};
-    const int nopts = (verbose && verbose[0] == '1') ? 5 : 4;
+                          regopt.c_str(), "--ptxas-options=-v"};
+    const int nopts = (verbose && verbose[0] == '1') ? 6 : 5;
     const nvrtcResult rc = nvrtcCompileProgram(prog, nopts, opts);
     size_t logn = 0;
     nvrtcGetProgramLogSize(prog, &logn);
     std::string log(logn, '\0');
     if (logn) nvrtcGetProgramLog(prog, &log[0]);
-    if (log_out) *log_out += log;
+    if (log_out) {
+      std::ostringstream gs;
+      gs << "side " << side << ": " << (g.cluster > 1 ? "cluster of " : "") << g.cluster << " CTA(s) x "
+         << g.block << " threads, " << g.ts << " slots per CTA row, " << g.spb << " shot(s) per CTA, "
+         << g.smem << " B shared memory, " << g.minblocks << " CTA(s) per SM, <= " << maxreg
+         << " registers\n";
+      *log_out += gs.str() + log;
+    }
     if (rc != NVRTC_SUCCESS) {
       nvrtcDestroyProgram(&prog);
       return LEAD_ECUDA;
@@ -122,6 +144,7 @@ int jit_compile(lead_code* code, std::string* log_out) {
     hs.bp_block = g.block;
     hs.bp_smem = g.smem;
     hs.bp_spb = g.spb;
+    hs.bp_cluster = g.cluster;
   }
   return LEAD_OK;
 }
@@ -136,7 +159,8 @@ int jit_load(lead_code* code) {
     if (cudaLibraryLoadData(&lib, hs.bp_cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess)
       return LEAD_ECUDA;
     int per_sm = 0;
-    if (cudaLibraryGetKernel(&kern, lib, "lead_bp_jit") != cudaSuccess ||
+    const char* name = hs.bp_cluster > 1 ? "lead_bp_jit_cluster" : "lead_bp_jit";
+    if (cudaLibraryGetKernel(&kern, lib, name) != cudaSuccess ||
         cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs.bp_smem) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, hs.bp_block, hs.bp_smem) !=
@@ -164,8 +188,9 @@ int jit_launch_bp(const lead_code* code, int side, const BPJitArgs& args, int sm
   const HostSide& hs = code->side[side];
   const DeviceSide& ds = code->dside[side];
   if (!ds.bp_func) return LEAD_ESTATE;
-  const long long groups = (args.shots + hs.bp_spb - 1) / hs.bp_spb;
-  const long long blocks = std::min<long long>(groups, (long long)sm_count * ds.bp_per_sm);
+  const long long groups = (args.shots + hs.bp_spb - 1) / hs.bp_spb;     // shots per CTA or per cluster
+  const long long units = std::max<long long>(1, ((long long)sm_count * ds.bp_per_sm) / hs.bp_cluster);
+  const long long blocks = std::min<long long>(groups, units) * hs.bp_cluster;
   BPJitArgs a = args;
   void* params[] = {&a};
   if (cudaLaunchKernel(ds.bp_func, dim3((unsigned)blocks), dim3(hs.bp_block), params, hs.bp_smem,

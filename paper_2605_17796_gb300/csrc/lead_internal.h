@@ -36,7 +36,8 @@ struct DeviceSide {
   int32_t* enumN1 = nullptr;     // 2^m_l x nl x (nl+1)
   uint64_t* ml = nullptr;        // 2^m_l least-weight coset members
   uint32_t* logicals = nullptr;  // k x words_n
-  uint16_t* bp_pa = nullptr;     // nl x (spb*order): partner shared-memory address | first << 15
+  uint16_t* bp_pa = nullptr;     // partner table of the min-sum kernel (u16 entries, or u32 with
+                                 // the owner rank for cluster launches)
   void* bp_module = nullptr;     // cudaLibrary_t of the specialised min-sum kernel
   void* bp_func = nullptr;       // its cudaKernel_t
   int bp_per_sm = 0;             // resident CTAs per SM
@@ -56,7 +57,7 @@ struct HostSide {
   int32_t kRA = 0, kRB = 0;
   SideParams params{};
   std::vector<char> bp_cubin;        // specialised min-sum kernel (NVRTC output)
-  int bp_block = 0, bp_spb = 0;
+  int bp_block = 0, bp_spb = 0, bp_cluster = 1;
   size_t bp_smem = 0;
 };
 
@@ -80,6 +81,11 @@ int prepare_device(lead_code* code, int device);
 void release_device(lead_code* code);
 int bp_shots_per_block(const lead_code* code);   // shots per CTA of the min-sum kernel
 struct BPJitArgs;
+struct Geometry {               // launch geometry of the min-sum kernel for one side
+  int spb, cluster, ts, block, minblocks;
+  size_t smem;
+};
+Geometry bp_geometry(const lead_code* code, int side);
 int jit_compile(lead_code* code, std::string* log);
 int jit_load(lead_code* code);
 void jit_unload(lead_code* code);

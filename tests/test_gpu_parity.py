@@ -29,7 +29,7 @@ def L():
 @pytest.fixture(scope="module")
 def codes(L):
     out = {}
-    for name in ("SL(2,3)", "PSL(2,7)"):
+    for name in ("SL(2,3)", "PSL(2,7)", "PSL(2,11)"):
         inst = workloads.standard(name, 0)
         out[name] = (inst, L.Code.from_instance(inst).prepare(0), tanner.from_instance(inst))
     return out
@@ -75,7 +75,7 @@ def test_local_table_bit_exact(codes, L, name, p):
         assert (got.view(np.uint32) == want.view(np.uint32)).all()
 
 
-@pytest.mark.parametrize("name", ["SL(2,3)", "PSL(2,7)"])
+@pytest.mark.parametrize("name", ["SL(2,3)", "PSL(2,7)", "PSL(2,11)"])
 @pytest.mark.parametrize("noise", [0, 1, 2])
 def test_sampler_bit_exact(codes, L, name, noise):
     inst, code, oc = codes[name]
@@ -125,7 +125,8 @@ def _syndromes(oc, side, shots, p, seed=0, offset=0):
 
 
 @pytest.mark.parametrize("name,side,p,shots", [("SL(2,3)", 0, 0.05, 45), ("SL(2,3)", 1, 0.08, 33),
-                                               ("PSL(2,7)", 0, 0.03, 21), ("PSL(2,7)", 1, 0.05, 19)])
+                                               ("PSL(2,7)", 0, 0.03, 21), ("PSL(2,7)", 1, 0.05, 19),
+                                               ("PSL(2,11)", 0, 0.03, 7)])
 def test_local_estimate_llr(codes, L, name, side, p, shots):
     inst, code, oc = codes[name]
     info = code.info
@@ -159,7 +160,9 @@ def _decode(L, code, oc, side, syn, p, alpha=1.0, max_iter=32, use_lead=True):
 @pytest.mark.parametrize("name,side,p,shots,use_lead", [
     ("SL(2,3)", 0, 0.04, 67, True), ("SL(2,3)", 1, 0.08, 41, True), ("SL(2,3)", 0, 0.06, 50, False),
     ("PSL(2,7)", 0, 0.01, 40, True), ("PSL(2,7)", 0, 0.02, 40, True), ("PSL(2,7)", 1, 0.03, 24, True),
-    ("PSL(2,7)", 0, 0.05, 12, True), ("PSL(2,7)", 0, 0.02, 20, False)])
+    ("PSL(2,7)", 0, 0.05, 12, True), ("PSL(2,7)", 0, 0.02, 20, False),
+    # |G| = 660: the decoder runs one shot per thread-block cluster
+    ("PSL(2,11)", 0, 0.03, 9, True), ("PSL(2,11)", 1, 0.02, 7, True), ("PSL(2,11)", 0, 0.02, 5, False)])
 def test_decode_bit_exact(codes, L, name, side, p, shots, use_lead):
     inst, code, oc = codes[name]
     info = code.info
@@ -209,11 +212,11 @@ def test_invalid_options_rejected(codes, L):
         assert e.value.rc == -1
 
 
-@pytest.mark.parametrize("name", ["SL(2,3)", "PSL(2,7)"])
+@pytest.mark.parametrize("name", ["SL(2,3)", "PSL(2,7)", "PSL(2,11)"])
 def test_check_flags_exact(codes, L, name):
     inst, code, oc = codes[name]
     info = code.info
-    shots = 60
+    shots = 60 if name != "PSL(2,11)" else 6
     for side in (0, 1):
         e, syn = _syndromes(oc, side, shots, 0.05, seed=17)
         wc, wst, wit, _ = olead.decode(oc, side, syn, 0.05)
