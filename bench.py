@@ -110,6 +110,31 @@ def _run_oracle(shots_per_p: int, seed: int = 0, offset: int = 0):
 
 # ------------------------------------------------------------------------------------------
 
+def _serving(lead, rate: float, n: int, code_psl7):
+    """p50/p99 latency of single-syndrome requests on the continuous-batching server: Poisson
+    arrivals, 70 % PSL(2,7) / 30 % PSL(2,11), depolarizing p = 0.03 (both sides decoded)."""
+    import numpy as np
+    import workloads
+    from paper_2605_17796_gb300 import serving as sv
+    code11 = lead.Code.from_instance(workloads.standard("PSL(2,11)", 0)).prepare(code_psl7.info.prepared_device)
+    codes = [code_psl7, code11]
+    p = 0.03
+    rng = np.random.default_rng(0)
+    arrival, code_of = sv.poisson_trace(rate, n, [0.7, 0.3], rng)
+    rows = [sv.request_rows(c, p, int((code_of == i).sum()), seed=100 + i) for i, c in enumerate(codes)]
+    srv = lead.Server(codes, [2 * p / 3] * 2, max_batch=256, streams=6, budget_bytes=2 << 30)
+    # warm-up: a short trace so every kernel is loaded before the measured one
+    warm_arr, warm_code = sv.poisson_trace(rate, 2000, [0.7, 0.3], np.random.default_rng(1))
+    warm_rows = [sv.request_rows(c, p, int((warm_code == i).sum()), seed=200 + i) for i, c in enumerate(codes)]
+    sv.run_trace(srv, warm_rows, warm_arr, warm_code)
+    res, _ = sv.run_trace(srv, rows, arrival, code_of)
+    srv.close()
+    out = sv.latency_stats(res, rate)
+    out.update({"mix": "70% PSL(2,7) / 30% PSL(2,11)", "noise": "depolarizing p=0.03, both sides",
+                "max_batch": 256, "streams": 6})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -121,6 +146,9 @@ def main():
     ap.add_argument("--oracle-shots-per-p", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-child", nargs=3, type=int)
+    ap.add_argument("--serving-rate", type=float, default=1e5)
+    ap.add_argument("--serving-requests", type=int, default=30000)
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
 
     if args.oracle_child:
@@ -306,6 +334,10 @@ def main():
                "sample": f"{args.oracle_shots_per_p} shots per p x 10 p values ({r['shots']} shots, "
                          f"{r['seconds']:.1f} s, numpy single-threaded)"}
 
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = _serving(lead, args.serving_rate, args.serving_requests, code)
+
     clocks = _clock_summary(clk_path, dev)
     ler = {f"{p:.2f}": r.failures / r.shots for p, r in zip(P_SWEEP, sweep)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -318,6 +350,7 @@ def main():
                        "l2": "inputs larger than L2 (2^20-shot chunks, 400 MB of errors)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "serving": serving,
             "clocks": clocks, "ler": ler,
             "mean_iters": {f"{p:.2f}": r.iters_sum / r.shots for p, r in zip(P_SWEEP, sweep)}}
     print(json.dumps(line))

@@ -262,6 +262,55 @@ int lead_decode_noalloc(const lead_code* code, const lead_decode_opts* opts, con
 int lead_check(const lead_code* code, int32_t side, const uint32_t* err, const uint32_t* corr,
                int64_t shots, uint8_t* fail, void* stream);
 
+/*
+ * Continuous-batching decode server (the serving loop of the workload; the paper has no serving
+ * layer). Requests are single shots of one of several codes prepared on the same device: both
+ * sides' syndromes, an id and an arrival time. A dispatcher thread inside the library admits
+ * each request once its arrival time has passed (times are nanoseconds on the server's clock,
+ * lead_server_clock_ns), groups ready requests of one code into a batch of at most max_batch
+ * shots whenever a stream slot is free, and keeps up to `streams` batches in flight (their
+ * kernels overlap on the device). Each slot owns device buffers for max_batch shots; the number
+ * of slots is min(streams, budget_bytes / slot size) (admission by memory; LEAD_EOOM if not even
+ * one fits). Every batch runs lead_decode on the sides in sides_mask and copies corrections and
+ * statuses back; completion is detected with cudaEventQuery. A result does not depend on the
+ * other requests of its batch (shots decode independently).
+ */
+typedef struct lead_server lead_server;
+
+typedef struct {
+  int32_t ncodes;
+  lead_code* const* codes;   /* prepared on one device                                        */
+  const double* p_side;      /* per code: channel marginal of each side (depolarizing p: 2p/3)  */
+  int32_t sides_mask;        /* bit 0: decode side 0, bit 1: decode side 1                       */
+  int32_t max_batch;         /* shots per launch                                                 */
+  int32_t streams;           /* batches in flight                                                */
+  size_t budget_bytes;       /* device memory the slots may use                                  */
+  int32_t max_iter;
+  float alpha;
+} lead_server_config;
+
+typedef struct {
+  uint64_t id;
+  int32_t code;
+  uint8_t status[2];         /* LEAD_ST_* per side (0 for a side not decoded)                    */
+  int64_t arrival_ns;        /* server clock                                                     */
+  int64_t done_ns;           /* when the dispatcher saw the batch complete                       */
+} lead_server_result;
+
+int lead_server_create(const lead_server_config* cfg, lead_server** out);
+/* n requests of code `code`: syn (host) rows of words_m[0] + words_m[1] words (side 0 then
+ * side 1), ids (host), arrival_ns (host, nullable = now). Copies the data; returns at once. */
+int lead_server_submit(lead_server* s, int32_t code, int64_t n, const uint32_t* syn, const uint64_t* ids,
+                       const int64_t* arrival_ns);
+/* Up to max completed results; corr (host, nullable) receives 2 x W words per result, W = the
+ * largest words_n of the server's codes (side 0 row, then side 1 row). *got = results written. */
+int lead_server_poll(lead_server* s, lead_server_result* out, uint32_t* corr, int64_t max, int64_t* got);
+/* Requests submitted but not yet returned by lead_server_poll's queue (scheduled, ready, in flight). */
+int lead_server_pending(lead_server* s, int64_t* pending);
+int lead_server_clock_ns(lead_server* s, int64_t* t);
+/* Stops the dispatcher, waits for the in-flight batches and frees the slots. */
+void lead_server_destroy(lead_server* s);
+
 /* Human-readable name of a status code (static string). */
 const char* lead_status_string(int status);
 

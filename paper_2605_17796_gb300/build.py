@@ -19,7 +19,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["device.cu", "sample.cu", "decode.cu"]
-CPP_SOURCES = ["code.cpp", "jit.cpp"]
+CPP_SOURCES = ["code.cpp", "jit.cpp", "server.cpp"]
 # the run-time specialised min-sum kernel: these files are embedded (in this order) as text
 JIT_SOURCES = ["bp_jit_args.h", "lead_math.cuh", "bp_jit_kernel.cuh"]
 CUDA_HOME = "/usr/local/cuda"
@@ -71,7 +71,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         jobs.append((cmd, obj))
     for src in CPP_SOURCES:
         obj = os.path.join(BUILD, src.replace(".cpp", ".o"))
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", BUILD,
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE, "-I", BUILD,
                "-I", os.path.join(CUDA_HOME, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
         jobs.append((cmd, obj))
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:

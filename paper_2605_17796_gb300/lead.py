@@ -40,6 +40,18 @@ class LeadDecodeOpts(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("alpha", ctypes.c_float), ("p", ctypes.c_double)]
 
 
+class LeadServerConfig(ctypes.Structure):
+    _fields_ = [("ncodes", ctypes.c_int32), ("codes", ctypes.POINTER(ctypes.c_void_p)),
+                ("p_side", ctypes.POINTER(ctypes.c_double)), ("sides_mask", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32), ("budget_bytes", ctypes.c_size_t),
+                ("max_iter", ctypes.c_int32), ("alpha", ctypes.c_float)]
+
+
+class LeadServerResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("code", ctypes.c_int32), ("status", ctypes.c_uint8 * 2),
+                ("arrival_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
 EXPORTS = {
     "lead_build_code": (ctypes.c_int, [ctypes.POINTER(LeadGroup), _c_int32_p, _c_int32_p, ctypes.c_int32,
                                        _c_uint8_p, ctypes.c_int32, _c_uint8_p, ctypes.c_int32,
@@ -70,6 +82,14 @@ EXPORTS = {
     "lead_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lead_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lead_server_create": (ctypes.c_int, [ctypes.POINTER(LeadServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
+    "lead_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "lead_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadServerResult), ctypes.c_void_p,
+                                        ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "lead_server_pending": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "lead_server_clock_ns": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "lead_server_destroy": (None, [ctypes.c_void_p]),
 }
 
 
@@ -248,3 +268,61 @@ def opts(side: int = 0, p: float = 0.05, alpha: float = 1.0, max_iter: int = 32,
          precision: int = PREC_FP32) -> LeadDecodeOpts:
     return LeadDecodeOpts(side=side, use_lead=1 if use_lead else 0, max_iter=max_iter, precision=precision,
                           alpha=alpha, p=p)
+
+
+class Server:
+    """Continuous-batching decode server (lead_server_*): submit single-shot requests with arrival
+    times, poll results. Codes must be prepared on the same device."""
+
+    def __init__(self, codes, p_side, sides_mask: int = 3, max_batch: int = 256, streams: int = 4,
+                 budget_bytes: int = 1 << 30, max_iter: int = 32, alpha: float = 1.0):
+        self.codes = list(codes)
+        self._handles = (ctypes.c_void_p * len(self.codes))(*[c._h.value for c in self.codes])
+        self._p = (ctypes.c_double * len(self.codes))(*p_side)
+        cfg = LeadServerConfig(ncodes=len(self.codes), codes=self._handles, p_side=self._p, sides_mask=sides_mask,
+                               max_batch=max_batch, streams=streams, budget_bytes=budget_bytes, max_iter=max_iter,
+                               alpha=alpha)
+        out = ctypes.c_void_p()
+        _check("lead_server_create", LIB.lead_server_create(ctypes.byref(cfg), ctypes.byref(out)))
+        self._h = out
+        self.W = max(c.info.words_n for c in self.codes)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            LIB.lead_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def clock_ns(self) -> int:
+        t = ctypes.c_int64()
+        _check("lead_server_clock_ns", LIB.lead_server_clock_ns(self._h, ctypes.byref(t)))
+        return t.value
+
+    def submit(self, code: int, syn: np.ndarray, ids: np.ndarray, arrival_ns: np.ndarray | None = None):
+        """syn: (n, words_m[0] + words_m[1]) uint32 host rows (side 0 then side 1)."""
+        syn = np.ascontiguousarray(syn, dtype=np.uint32)
+        ids = np.ascontiguousarray(ids, dtype=np.uint64)
+        arr = None if arrival_ns is None else np.ascontiguousarray(arrival_ns, dtype=np.int64)
+        _check("lead_server_submit", LIB.lead_server_submit(self._h, code, len(ids), syn.ctypes.data, ids.ctypes.data,
+                                                            None if arr is None else arr.ctypes.data))
+
+    def poll(self, max_results: int = 65536):
+        """Returns (results structured array, corrections (k, 2, W) uint32)."""
+        out = (LeadServerResult * max_results)()
+        corr = np.zeros((max_results, 2, self.W), dtype=np.uint32)
+        got = ctypes.c_int64()
+        _check("lead_server_poll", LIB.lead_server_poll(self._h, out, corr.ctypes.data, max_results, ctypes.byref(got)))
+        k = got.value
+        res = np.zeros(k, dtype=[("id", np.uint64), ("code", np.int32), ("status", np.uint8, 2),
+                                 ("arrival_ns", np.int64), ("done_ns", np.int64)])
+        for i in range(k):
+            r = out[i]
+            res[i] = (r.id, r.code, tuple(r.status), r.arrival_ns, r.done_ns)
+        return res, corr[:k]
+
+    def pending(self) -> int:
+        p = ctypes.c_int64()
+        _check("lead_server_pending", LIB.lead_server_pending(self._h, ctypes.byref(p)))
+        return p.value

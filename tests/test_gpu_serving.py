@@ -1,0 +1,99 @@
+"""The continuous-batching decode server: every result equals the batch decode of the same shot,
+whether the request was served alone or mixed with other codes' traffic; memory admission."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def setup():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2605_17796_gb300 import lead, serving
+    codes = [lead.Code.from_instance(workloads.standard(n, 0)).prepare(0) for n in ("SL(2,3)", "PSL(2,7)")]
+    p = 0.03
+    rows = [serving.request_rows(c, p, 150, seed=21 + i) for i, c in enumerate(codes)]
+    # reference: one batch decode per code and side, with the same options as the server
+    ref = []
+    for c, r in zip(codes, rows):
+        info = c.info
+        n = r.shape[0]
+        out = {}
+        for side in (0, 1):
+            off = 0 if side == 0 else info.words_m[0]
+            syn = torch.from_numpy(np.ascontiguousarray(r[:, off:off + info.words_m[side]]).view(np.int32)).cuda()
+            o = lead.opts(side=side, p=2 * p / 3)
+            ws = torch.zeros(c.workspace_bytes(o) // 4 + 64, dtype=torch.int32, device="cuda")
+            corr = torch.zeros((n, info.words_n), dtype=torch.int32, device="cuda")
+            st = torch.zeros(n, dtype=torch.uint8, device="cuda")
+            c.decode(o, syn, n, corr, st, workspace=ws)
+            out[side] = (corr.cpu().numpy().view(np.uint32), st.cpu().numpy())
+        ref.append(out)
+    torch.cuda.synchronize()
+    return lead, serving, codes, rows, ref, p
+
+
+def _check(res, cor, codes, ref, key_of):
+    W = max(c.info.words_n for c in codes)
+    for k in range(len(res)):
+        c, i = key_of(int(res["id"][k]))
+        wn = codes[c].info.words_n
+        for side in (0, 1):
+            assert res["status"][k][side] == ref[c][side][1][i]
+            assert (cor[k, side, :wn] == ref[c][side][0][i]).all()
+            assert not cor[k, side, wn:W].any()
+
+
+def test_mixed_traffic_matches_batch_decode(setup):
+    lead, serving, codes, rows, ref, p = setup
+    srv = lead.Server(codes, [2 * p / 3] * 2, max_batch=32, streams=3, budget_bytes=256 << 20)
+    rng = np.random.default_rng(0)
+    n = sum(r.shape[0] for r in rows)
+    arrival, code_of = serving.poisson_trace(2e5, n, [0.5, 0.5], rng)
+    # use every row of both codes exactly once
+    code_of = np.array([0] * rows[0].shape[0] + [1] * rows[1].shape[0], dtype=np.int32)[rng.permutation(n)]
+    res, cor = serving.run_trace(srv, rows, arrival, code_of)
+    idx = np.zeros(n, dtype=np.int64)
+    for c in (0, 1):
+        sel = np.nonzero(code_of == c)[0]
+        idx[sel] = np.arange(sel.size)
+    _check(res, cor, codes, ref, lambda rid: (int(code_of[rid]), int(idx[rid])))
+    assert srv.pending() == 0
+    srv.close()
+
+
+def test_alone_equals_in_the_mix(setup):
+    lead, serving, codes, rows, ref, p = setup
+    srv = lead.Server(codes, [2 * p / 3] * 2, max_batch=32, streams=2, budget_bytes=256 << 20)
+    for c in (0, 1):
+        for i in (0, 7, 42):
+            srv.submit(c, rows[c][i:i + 1], np.array([1000 * c + i], dtype=np.uint64))
+            got = []
+            import time
+            t_end = time.time() + 30
+            while not got and time.time() < t_end:
+                r, cr = srv.poll()
+                if len(r):
+                    got = [(r, cr)]
+            r, cr = got[0]
+            assert len(r) == 1 and int(r["id"][0]) == 1000 * c + i
+            _check(r, cr, codes, ref, lambda rid: (rid // 1000, rid % 1000))
+    srv.close()
+
+
+def test_memory_admission(setup):
+    lead, serving, codes, rows, ref, p = setup
+    with pytest.raises(lead.LeadError) as e:
+        lead.Server(codes, [2 * p / 3] * 2, max_batch=1024, streams=4, budget_bytes=1 << 16)
+    assert e.value.rc == -5           # LEAD_EOOM: not even one slot fits the budget
+    # a small budget admits fewer slots and still serves every request
+    srv = lead.Server(codes, [2 * p / 3] * 2, max_batch=8, streams=4, budget_bytes=400_000)
+    arrival, _ = serving.poisson_trace(1e5, 20, [1.0], np.random.default_rng(1))
+    res, cor = serving.run_trace(srv, [rows[0][:20], rows[1][:0]], arrival, np.zeros(20, dtype=np.int32))
+    _check(res, cor, codes, ref, lambda rid: (0, rid))
+    srv.close()
