@@ -1,0 +1,150 @@
+"""Several codes with uneven shot counts decoded by one CUDA-graph launch.
+
+Each entry (code, shots, noise, p, seed) runs the full pipeline -- sample, decode every side the
+noise touches, check -- on its own stream (or a stream the plan assigns), split into chunks; the
+streams fork from and join back to the capturing stream, so their kernels overlap on the
+device. The whole batch is captured once into a CUDA graph and replayed with one launch.
+A plan (stream of every entry, chunks per entry) is chosen by `autotune`, which captures each
+candidate plan and keeps the one with the shortest replay.
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass
+
+import torch
+
+from . import lead
+
+
+@dataclass
+class Entry:
+    code: lead.Code
+    shots: int
+    noise: int = lead.NOISE_DEPOL
+    p: float = 0.04
+    seed: int = 0
+    offset: int = 0
+
+
+class MultiCodeBatch:
+    def __init__(self, entries, plan=None, alpha: float = 1.0, max_iter: int = 32):
+        self.entries = list(entries)
+        self.alpha, self.max_iter = alpha, max_iter
+        # plan: list of (stream index, chunks) per entry; default = own stream, one chunk
+        self.plan = plan or [(i, 1) for i in range(len(self.entries))]
+        self.device = torch.device("cuda", self.entries[0].code.info.prepared_device)
+        nstreams = max(s for s, _ in self.plan) + 1
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(nstreams)]
+        self.buf = []
+        for e in self.entries:
+            info = e.code.info
+            kw = dict(device=self.device)
+            b = {"err": [torch.zeros((e.shots, info.words_n), dtype=torch.int32, **kw) for _ in range(2)],
+                 "syn": [torch.zeros((e.shots, info.words_m[s]), dtype=torch.int32, **kw) for s in range(2)],
+                 "corr": [torch.zeros((e.shots, info.words_n), dtype=torch.int32, **kw) for _ in range(2)],
+                 "status": [torch.zeros(e.shots, dtype=torch.uint8, **kw) for _ in range(2)],
+                 "iters": [torch.zeros(e.shots, dtype=torch.int32, **kw) for _ in range(2)],
+                 "fail": [torch.zeros(e.shots, dtype=torch.uint8, **kw) for _ in range(2)]}
+            ws = max(e.code.workspace_bytes(lead.opts(side=s)) for s in range(2))
+            b["ws"] = [torch.zeros(ws // 4 + 64, dtype=torch.int32, **kw) for _ in range(2)]
+            self.buf.append(b)
+        self.graph = None
+
+    @staticmethod
+    def sides(noise):
+        return {lead.NOISE_X: [0], lead.NOISE_Z: [1], lead.NOISE_DEPOL: [0, 1]}[noise]
+
+    def _entry_work(self, i, stream):
+        e, b = self.entries[i], self.buf[i]
+        sides = self.sides(e.noise)
+        chunks = self.plan[i][1]
+        step = -(-e.shots // chunks)
+        p_side = e.p if e.noise != lead.NOISE_DEPOL else 2.0 * e.p / 3.0
+        for c0 in range(0, e.shots, step):
+            n = min(step, e.shots - c0)
+            sl = slice(c0, c0 + n)
+            e.code.sample(e.noise, e.p, n, e.seed, e.offset + c0,
+                          err_x=b["err"][0][sl] if 0 in sides else None, err_z=b["err"][1][sl] if 1 in sides else None,
+                          syn_z=b["syn"][0][sl] if 0 in sides else None, syn_x=b["syn"][1][sl] if 1 in sides else None,
+                          stream=stream)
+            for s in sides:
+                o = lead.opts(side=s, p=p_side, alpha=self.alpha, max_iter=self.max_iter)
+                e.code.decode(o, b["syn"][s][sl], n, b["corr"][s][sl], b["status"][s][sl], b["iters"][s][sl],
+                              workspace=b["ws"][s], stream=stream)
+                e.code.check(s, b["err"][s][sl], b["corr"][s][sl], n, b["fail"][s][sl], stream=stream)
+
+    def issue(self):
+        """Enqueue the whole batch: fork the plan's streams from the current stream and join them."""
+        main = torch.cuda.current_stream(self.device)
+        for st in self.streams:
+            st.wait_stream(main)
+        for i in range(len(self.entries)):
+            st = self.streams[self.plan[i][0]]
+            with torch.cuda.stream(st):
+                self._entry_work(i, st)
+        for st in self.streams:
+            main.wait_stream(st)
+
+    def capture(self):
+        self.issue()                                   # eager run: loads kernels, sets attributes
+        torch.cuda.synchronize(self.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="relaxed"):
+            self.issue()
+        torch.cuda.synchronize(self.device)
+        return self
+
+    def replay(self):
+        self.graph.replay()
+
+    def time_replays(self, reps: int = 3) -> float:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        self.replay()
+        torch.cuda.synchronize(self.device)
+        e0.record()
+        for _ in range(reps):
+            self.replay()
+        e1.record()
+        torch.cuda.synchronize(self.device)
+        return e0.elapsed_time(e1) / reps
+
+    def summary(self):
+        out = []
+        for e, b in zip(self.entries, self.buf):
+            sides = self.sides(e.noise)
+            fail = torch.zeros(e.shots, dtype=torch.bool, device=self.device)
+            for s in sides:
+                fail |= b["fail"][s] != 0
+            out.append({"shots": e.shots, "n": e.code.info.n, "failures": int(fail.sum()),
+                        "mean_iters": float(sum(b["iters"][s].double().mean() for s in sides) / len(sides))})
+        return out
+
+
+def candidate_plans(n_entries: int, heavy: int):
+    """Plans to try: every entry on its own stream or all on one, with the heaviest entry split
+    into 1, 2 or 4 chunks (on its stream, or spread over extra streams)."""
+    plans = []
+    for one_stream, chunks in itertools.product((False, True), (1, 2, 4)):
+        plan = [(0 if one_stream else i, 1) for i in range(n_entries)]
+        plan[heavy] = (plan[heavy][0], chunks)
+        plans.append(plan)
+    return plans
+
+
+def autotune(entries, reps: int = 2, **kw):
+    """Capture every candidate plan and return (best batch, [(plan, ms)])."""
+    work = [e.shots * e.code.info.n for e in entries]
+    heavy = max(range(len(entries)), key=lambda i: work[i])
+    best, timings = None, []
+    for plan in candidate_plans(len(entries), heavy):
+        b = MultiCodeBatch(entries, plan=plan, **kw).capture()
+        ms = b.time_replays(reps)
+        timings.append((plan, ms))
+        if best is None or ms < best[1]:
+            best = (b, ms)
+        else:
+            del b
+        torch.cuda.empty_cache()
+    return best[0], timings
