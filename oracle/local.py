@@ -361,3 +361,77 @@ def boosted_table_f32(N, N1, ml_mask, p: float) -> np.ndarray:
     n_l = q.shape[1]
     flip = ((ml_mask[:, None] >> np.arange(n_l)[None, :]) & 1).astype(bool)
     return np.where(flip, np.maximum(q, np.float32(0.5)), q).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------------------
+# Per-qubit (non-uniform) priors. The defining sums are the same, with pi(e) the product of the
+# qubits' own Bernoulli priors p_j. They are evaluated by the row grouping of the module doc in
+# FP64, with row weights relative to the all-zero row: r_a(x) = prod_{b: x_b = 1} p_ab/(1 - p_ab).
+# The hard decision is the ML member, the least cost sum_j e_j W_j with integer costs
+# W_j = rint(2^20 * lambda_f32(p_j)) (exact sums, so uniform priors reproduce the integer-weight
+# decision), ties broken by the least row-major key as in the uniform case.
+# ---------------------------------------------------------------------------------------
+
+def coset_row_images(RA: np.ndarray, RB: np.ndarray, s: int):
+    """All row-image matrices F (as (Delta,) arrays of f_a) with R_A F = S, for syndrome s."""
+    fa, s_of_F = _row_images(RA, RB)
+    return fa[:, s_of_F == s]
+
+
+def posterior_nonuniform(RA: np.ndarray, RB: np.ndarray, s: int, p: np.ndarray) -> np.ndarray:
+    """q_j = P(e_j = 1 | H_v e = s) for per-position priors p (local index j = b*Delta + a), FP64."""
+    kA, delta = RA.shape
+    f_of_x, _, bits, _, _ = _row_tables(RB)
+    kB = RB.shape[0]
+    P = np.asarray(p, dtype=np.float64).reshape(delta, delta).T            # P[a][b] = p_{b*Delta + a}
+    odds = P / (1.0 - P)
+    R = np.zeros((delta, 1 << kB))
+    Rb = np.zeros((delta, delta, 1 << kB))
+    for a in range(delta):
+        w = np.prod(np.where(bits == 1, odds[a][None, :], 1.0), axis=1)      # r_a(x), x = 0..2^Delta-1
+        np.add.at(R[a], f_of_x, w)
+        for b in range(delta):
+            sel = bits[:, b] == 1
+            np.add.at(Rb[a, b], f_of_x[sel], w[sel])
+    F = coset_row_images(RA, RB, s)                                        # (Delta, #F)
+    terms = np.prod(np.stack([R[a][F[a]] for a in range(delta)]), axis=0)  # prod_a R_a(f_a)
+    Z = terms.sum()
+    q = np.zeros((delta, delta))
+    for a in range(delta):
+        others = terms / R[a][F[a]]
+        for b in range(delta):
+            q[a, b] = (others * Rb[a, b][F[a]]).sum() / Z
+    return q.T.reshape(-1)                                                 # back to j = b*Delta + a
+
+
+def integer_costs(p: np.ndarray) -> np.ndarray:
+    """W_j = rint(2^20 * lambda_f32(p_j)) as int64 (binary32 lambda, exact scaling, round half even)."""
+    lam = llr_f32(np.asarray(p, dtype=np.float32))
+    return np.rint((lam * np.float32(2 ** 20)).astype(np.float32)).astype(np.int64)
+
+
+def ml_nonuniform(RA: np.ndarray, RB: np.ndarray, s: int, W: np.ndarray) -> int:
+    """Least (sum_j e_j W_j, row-major key) coset member for integer costs W (local order j)."""
+    kA, delta = RA.shape
+    f_of_x, _, bits, _, _ = _row_tables(RB)
+    Wm = np.asarray(W, dtype=np.int64).reshape(delta, delta).T            # Wm[a][b]
+    F = coset_row_images(RA, RB, s)
+    kB = RB.shape[0]
+    best_row = np.zeros((delta, 1 << kB, 2), dtype=np.int64)               # (cost, least x) per class
+    for a in range(delta):
+        cost = bits @ Wm[a]
+        for f in range(1 << kB):
+            xs = np.nonzero(f_of_x == f)[0]
+            c = cost[xs]
+            m = c.min()
+            best_row[a, f] = (m, xs[c == m].min())
+    tot = sum(best_row[a, F[a], 0] for a in range(delta))
+    key = sum(best_row[a, F[a], 1] << (a * delta) for a in range(delta))
+    i = np.lexsort((key, tot))[0]
+    mask = 0
+    for a in range(delta):
+        x = int(best_row[a, F[a, i], 1])
+        for b in range(delta):
+            if (x >> b) & 1:
+                mask |= 1 << (b * delta + a)
+    return mask

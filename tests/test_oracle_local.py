@@ -189,3 +189,45 @@ def test_boost_applies_to_ml_bits(psl7):
     flip = ((ml[:, None] >> np.arange(36)[None, :]) & 1).astype(bool)
     assert (lut[flip] >= 0.5).all()
     assert (lut[~flip] == q[~flip]).all()
+
+
+def test_nonuniform_posterior_equals_defining_sum(sl3):
+    inst, code = sl3
+    rng = np.random.default_rng(5)
+    for side in code.sides:
+        for s in (0, 3, 9, 15):
+            p = rng.uniform(0.01, 0.3, 16)
+            got = local.posterior_nonuniform(side.RA, side.RB, s, p)
+            want = local.posterior_brute_force(side.L, s, p)
+            assert np.abs(got - want).max() < 1e-13
+
+
+def test_nonuniform_reduces_to_uniform(psl7):
+    inst, code = psl7
+    side = code.sides[0]
+    N, N1, ml = local.tables(side.RA, side.RB)
+    q = local.posterior_from_tables(N, N1, 0.04)
+    W = local.integer_costs(np.full(36, 0.04))
+    for s in (0, 5, 77, 300, 511):
+        got = local.posterior_nonuniform(side.RA, side.RB, s, np.full(36, 0.04))
+        assert np.abs(got - q[s]).max() < 1e-12
+        assert local.ml_nonuniform(side.RA, side.RB, s, W) == int(ml[s])
+
+
+def test_nonuniform_ml_is_least_cost_brute_force(sl3):
+    inst, code = sl3
+    side = code.sides[0]
+    rng = np.random.default_rng(9)
+    es = np.arange(1 << 16)
+    bits = ((es[:, None] >> np.arange(16)[None, :]) & 1)
+    syn = ((bits @ side.L.T.astype(np.int64)) & 1) @ (1 << np.arange(side.m_l))
+    for _ in range(20):
+        p = rng.uniform(0.005, 0.4, 16)
+        W = local.integer_costs(p)
+        s = int(rng.integers(0, 1 << side.m_l))
+        sel = es[syn == s]
+        cost = bits[syn == s] @ W
+        # least cost, ties by the row-major key (local j = b*Delta + a -> key bit a*Delta + b)
+        key = sum(((sel >> (b * 4 + a)) & 1) << (a * 4 + b) for a in range(4) for b in range(4))
+        want = int(sel[np.lexsort((key, cost))[0]])
+        assert local.ml_nonuniform(side.RA, side.RB, s, W) == want
