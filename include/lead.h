@@ -253,6 +253,52 @@ int lead_decode_noalloc(const lead_code* code, const lead_decode_opts* opts, con
                         float* llr, void* stream);
 
 /*
+ * Per-qubit priors. Algorithm 1 Phase 1 assumes the channel marginal p for every qubit; these
+ * entry points take instead one prior probability per qubit and shot (e.g. from soft
+ * measurement information), and compute the exact local posterior of every view under the
+ * product of its qubits' priors:
+ *   q_j = sum_{E in coset(s_v)} [E_j = 1] prod_i p_i^{E_i} (1-p_i)^{1-E_i} / (same sum without [E_j = 1]).
+ * The coset is grouped by row images: a view's local error E (rows a, columns b, local index
+ * j = b*Delta + a) has local syndrome R_A F with F = (R_B x_a)_a, x_a the row patterns, so
+ * the sum runs over the 2^(Delta k_B - m_l) row-image matrices F of the coset and, per row, over
+ * the patterns of each image. Binary32 arithmetic with log-sum-exp per row class (relative
+ * error of q about 1e-5). The hard decision boosted to 1/2 (Algorithm 1 Phase 1) is the least
+ * integer cost sum_j E_j W_j, W_j = rint(2^20 lambda(p_j)) with lambda the binary32 prior LLR
+ * of lead_decode's decision track, ties broken by the least key sum_{a,b} E[a][b] 2^(a Delta + b).
+ * Phase 2 merges the two views' boosted posteriors as lead_decode does.
+ * Supported local codes: (Delta, k_B, m_l) = (6, 3, 9) and (4, 2, 4); others give LEAD_EINVAL.
+ * opts->p is not used; opts->alpha, side, max_iter and use_lead are.
+ *  prior (dev, shots x n float): p_i per shot and qubit, clamped to [2^-23, 1 - 2^-23].
+ * The work runs in passes of at most ~256 MiB of local posteriors and prior LLRs.
+ */
+size_t lead_priors_workspace_bytes(const lead_code* code, const lead_decode_opts* opts, int64_t shots);
+
+/*
+ * lead_local_estimate_priors -- Phases 1-2 with per-qubit priors.
+ *  llr    (dev, shots x n float) merged prior LLRs of the global decoder.
+ *  q_out  (dev, shots x |G| x Delta^2 float, nullable) boosted local posteriors per view
+ *         ([shot][vertex][j]); when NULL, the workspace holds them one pass at a time.
+ *  ml_out (dev, shots x |G| uint64, nullable) the least-cost local decision of every view
+ *         (bit j = local index j).
+ *  workspace (dev, 16-byte aligned) >= lead_priors_workspace_bytes(opts, shots) unless q_out.
+ * Errors: LEAD_EINVAL, LEAD_ESTATE, LEAD_ECUDA.
+ */
+int lead_local_estimate_priors(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn,
+                               int64_t shots, const float* prior, float* llr, float* q_out, uint64_t* ml_out,
+                               void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * lead_decode_priors -- Algorithm 1 with per-qubit priors: Phases 1-2 as
+ * lead_local_estimate_priors (opts->use_lead == 1), or the prior LLR lambda(p_i) of every qubit
+ * (the standalone min-sum baseline, use_lead == 0), then lead_decode's global min-sum.
+ *  Outputs as lead_decode. workspace (dev, 16-byte aligned) >= lead_priors_workspace_bytes.
+ * Errors: LEAD_EINVAL, LEAD_ESTATE, LEAD_ECUDA.
+ */
+int lead_decode_priors(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn, int64_t shots,
+                       const float* prior, uint32_t* corr, uint8_t* status, int32_t* iters, float* llr,
+                       void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * lead_check -- success test of Sec. IV-A on one side: residual r = err + corr.
  *  fail[shot] (dev uint8): bit 0 set iff H r != 0 (the correction misses the syndrome);
  *  bit 1 set iff H r = 0 and r is a nontrivial logical operator (it anticommutes with one of

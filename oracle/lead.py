@@ -95,6 +95,39 @@ def channel_prior_f32(n: int, shots: int, p: float) -> np.ndarray:
     return np.broadcast_to(local.llr_f32(np.array([p], dtype=np.float32)), (shots, n)).copy()
 
 
+def local_priors(code: TannerCode, side_id: int, syn: np.ndarray, prior: np.ndarray, boost: bool = True):
+    """Phase 1 with per-qubit priors: local posteriors q (S, |G|, n_l) in FP64, boosted to 1/2 on
+    the bits of the least-cost local decision unless boost=False, and those decisions (S, |G|) as
+    masks (bit j = local index j). prior (S, n)."""
+    side = code.sides[side_id]
+    sv = local_syndromes(side, syn)
+    S, V = sv.shape
+    nl = side.views.shape[1]
+    q = np.zeros((S, V, nl))
+    ml = np.zeros((S, V), dtype=np.int64)
+    for s in range(S):
+        for v in range(V):
+            pv = prior[s, side.views[v]]
+            qq = local.posterior_nonuniform(side.RA, side.RB, int(sv[s, v]), pv.astype(np.float64))
+            m = local.ml_nonuniform(side.RA, side.RB, int(sv[s, v]), local.integer_costs(pv))
+            flip = ((m >> np.arange(nl)) & 1).astype(bool)
+            q[s, v] = np.where(flip, np.maximum(qq, 0.5), qq) if boost else qq
+            ml[s, v] = m
+    return q, ml
+
+
+def merge_priors_f32(code: TannerCode, side_id: int, q: np.ndarray, alpha: float = 1.0) -> np.ndarray:
+    """Phase 2 on per-view boosted posteriors q (S, |G|, n_l), binary32 decision track:
+    lambda(alpha * ((q0 + q1) * 1/2)) per qubit, q rounded to binary32 first."""
+    qv = code.sides[side_id].qubit_views
+    q32 = q.astype(np.float32)
+    q0 = q32[:, qv[:, 0, 0], qv[:, 0, 1]]
+    q1 = q32[:, qv[:, 1, 0], qv[:, 1, 1]]
+    h = (q0 + q1).astype(np.float32)
+    h = (h * np.float32(0.5)).astype(np.float32)
+    return local.llr_f32((h * np.float32(alpha)).astype(np.float32))
+
+
 class _Graph:
     """Edge lists of a check matrix whose rows come in consecutive blocks of ``block`` rows
     (the checks of one vertex). For every qubit, its edges are grouped by block in increasing

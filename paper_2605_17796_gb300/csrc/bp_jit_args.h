@@ -21,6 +21,7 @@ struct BPJitArgs {
   int* iters;
   float* llr;
   const float* table;           // 2^m_l x nl local posterior table (nullptr for the baseline)
+  const float* lam;             // shots x n per-qubit prior LLRs; when set, the prior of every slot
   const unsigned short* pa;     // [j][t] partner shared-memory address | first view << 15
   const unsigned short* views;  // [v][j] qubit index
   const float* llr_t0;          // prior-LLR interpolation table: node values

@@ -64,7 +64,9 @@ lead_bp_jit(const lead::BPJitArgs a) {
       sv = lead::bit_field(srow, v * ML, ML);
 #pragma unroll 2
       for (int j = 0; j < NL; ++j) {
-        if (a.use_lead) {
+        if (a.lam) {
+          Ls[j * TS + tid] = __ldg(a.lam + (g0 + sl) * a.n + __ldg(a.views + v * NL + j));
+        } else if (a.use_lead) {
           const unsigned int addr = __ldg(PA + j * TS + tid) & 0x7FFFu;
           const unsigned int jp = addr / TS, vp = addr - jp * TS - sl * V;
           const unsigned int svp = lead::bit_field(srow, vp * ML, ML);
@@ -266,7 +268,9 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
       sv = lead::bit_field(syn_s, v * ML, ML);
 #pragma unroll 2
       for (int j = 0; j < NL; ++j) {
-        if (a.use_lead) {
+        if (a.lam) {
+          Ls[j * TS + tid] = __ldg(a.lam + g0 * a.n + __ldg(a.views + v * NL + j));
+        } else if (a.use_lead) {
           const unsigned int pa = __ldg(PA + j * V + v);
           const unsigned int addr = pa & 0xFFFFu, pr = (pa >> 16) & 0xFFu;
           const unsigned int jp = addr / TS, vp = pr * TS + (addr - jp * TS);

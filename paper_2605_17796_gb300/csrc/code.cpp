@@ -66,6 +66,48 @@ std::vector<uint8_t> masks_to_bytes(const std::vector<uint64_t>& m, int cols) {
   return out;
 }
 
+// Row grouping of the local code kron(R_B, R_A) (per-qubit-prior posterior, Algorithm 1 Phase 1):
+// a local error E (rows a, columns b) has syndrome S = R_A F with F = (R_B x_a)_a the row images,
+// so the coset of S is the set of row-image matrices F with R_A F = S, each combined with any
+// row patterns of those images. Stores the class members, the least F of every syndrome and the
+// F of zero syndrome; left empty where the tables would be too large.
+void row_grouping(lead::HostSide& hs, const std::vector<uint64_t>& RA, const std::vector<uint64_t>& RB,
+                  int delta) {
+  hs.xcls.clear();
+  hs.cbase.clear();
+  hs.ckern.clear();
+  const int kA = hs.kRA, kB = hs.kRB;
+  if (delta * kB > 24 || kB >= delta) return;
+  const int NX = 1 << delta, NF = 1 << kB;
+  std::vector<int> fx(NX, 0);
+  for (int x = 0; x < NX; ++x)
+    for (int rB = 0; rB < kB; ++rB)
+      if (__builtin_popcountll(RB[rB] & (uint64_t)x) & 1) fx[x] |= 1 << rB;
+  for (int f = 0; f < NF; ++f) {
+    size_t before = hs.xcls.size();
+    for (int x = 0; x < NX; ++x)
+      if (fx[x] == f) hs.xcls.push_back((uint8_t)x);
+    if (hs.xcls.size() - before != (size_t)(NX / NF)) {   // R_B rank-deficient: classes uneven
+      hs.xcls.clear();
+      return;
+    }
+  }
+  // bit (rB*kA + rA) of S is the parity of F over the bits a*kB + rB with RA[rA] bit a set
+  std::vector<uint32_t> smask(kA * kB, 0);
+  for (int rA = 0; rA < kA; ++rA)
+    for (int rB = 0; rB < kB; ++rB)
+      for (int a = 0; a < delta; ++a)
+        if ((RA[rA] >> a) & 1) smask[rB * kA + rA] |= 1u << (a * kB + rB);
+  hs.cbase.assign((size_t)1 << hs.m_l, 0xFFFFFFFFu);
+  const uint32_t NFF = 1u << (delta * kB);
+  for (uint32_t F = 0; F < NFF; ++F) {
+    uint32_t S = 0;
+    for (int r = 0; r < kA * kB; ++r) S |= (uint32_t)(__builtin_popcount(F & smask[r]) & 1) << r;
+    if (hs.cbase[S] == 0xFFFFFFFFu) hs.cbase[S] = F;
+    if (S == 0) hs.ckern.push_back(F);
+  }
+}
+
 // ---- large GF(2) matrices: packed rows of `words` 64-bit words ------------------------------
 
 inline bool bit(const Row& r, int c) { return (r[c >> 6] >> (c & 63)) & 1; }
@@ -266,6 +308,7 @@ int build(const lead_group* G, const int32_t* A, const int32_t* B, int32_t delta
         hs.max_row_weight = std::max(hs.max_row_weight, __builtin_popcountll(msk));
       }
     if (hs.max_row_weight > lead::kMaxSupport) return LEAD_EINVAL;
+    row_grouping(hs, RA, RB, delta);
     // views
     hs.views.assign((size_t)order * nl, 0);
     for (int v = 0; v < order; ++v)

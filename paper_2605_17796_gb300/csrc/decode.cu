@@ -147,9 +147,13 @@ int launch_local(const lead_code* code, const lead_decode_opts* o, const uint32_
   return LEAD_EINVAL;
 }
 
+}  // namespace
+
+// The min-sum kernel (Phase 3) on one side. Its prior: per-qubit LLRs lam_in (shots x n) when
+// given, else the merged local posteriors of `table` (use_lead), else the channel LLR.
 int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* syn, int64_t shots,
               uint32_t* corr, uint8_t* status, int32_t* iters, float* llr, const float* table,
-              cudaStream_t stream) {
+              cudaStream_t stream, const float* lam_in) {
   BPJitArgs a{};
   a.n = code->n;
   a.words_n = code->words_n;
@@ -167,6 +171,7 @@ int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* 
   a.iters = iters;
   a.llr = llr;
   a.table = table;
+  a.lam = lam_in;
   a.pa = code->dside[o->side].bp_pa;
   a.views = code->dside[o->side].views;
   a.llr_t0 = code->d_llr;
@@ -175,7 +180,6 @@ int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* 
   return jit_launch_bp(code, o->side, a, sm_count(code->device), stream);
 }
 
-}  // namespace
 }  // namespace lead
 
 extern "C" {
@@ -225,7 +229,7 @@ int lead_decode(const lead_code* code, const lead_decode_opts* opts, const uint3
     rc = launch_table(code, opts->side, opts->p, table, s);
     if (rc != LEAD_OK) return rc;
   }
-  return launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s);
+  return launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s, nullptr);
 }
 
 }  // extern "C"
@@ -290,5 +294,5 @@ extern "C" int lead_decode_noalloc(const lead_code* code, const lead_decode_opts
     rc = launch_table(code, opts->side, opts->p, table, s);
     if (rc != LEAD_OK) return rc;
   }
-  return launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s);
+  return launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s, nullptr);
 }

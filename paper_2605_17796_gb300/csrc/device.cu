@@ -162,6 +162,9 @@ int prepare_side(lead_code* code, int s) {
   LEAD_TRY(upload(&ds.partner, hs.partner));
   LEAD_TRY(upload(&ds.qslots, hs.qslots));
   LEAD_TRY(upload(&ds.logicals, hs.logicals));
+  LEAD_TRY(upload(&ds.xcls, hs.xcls));
+  LEAD_TRY(upload(&ds.cbase, hs.cbase));
+  LEAD_TRY(upload(&ds.ckern, hs.ckern));
   // min-sum kernel partner table. One CTA per shot group: thread t = shot sl * order + vertex v,
   // slot (j, t) lives at shared-memory word j * ts + t; entry = partner address | first << 15.
   // Cluster launch: CTA rank r owns vertices r*ts .. r*ts + ts - 1; entry (u32, indexed [j][v]) =
@@ -283,6 +286,9 @@ void release_device(lead_code* code) {
     cudaFree(ds.ml);
     cudaFree(ds.logicals);
     cudaFree(ds.bp_pa);
+    cudaFree(ds.xcls);
+    cudaFree(ds.cbase);
+    cudaFree(ds.ckern);
     ds = DeviceSide{};
   }
   cudaFree(code->d_llr);

@@ -38,6 +38,9 @@ struct DeviceSide {
   uint32_t* logicals = nullptr;  // k x words_n
   uint16_t* bp_pa = nullptr;     // partner table of the min-sum kernel (u16 entries, or u32 with
                                  // the owner rank for cluster launches)
+  uint8_t* xcls = nullptr;       // row patterns of every class f = R_B x (class-major, increasing)
+  uint32_t* cbase = nullptr;     // 2^m_l: one row-image matrix F with R_A F = S per local syndrome
+  uint32_t* ckern = nullptr;     // row-image matrices with R_A F = 0, increasing
   void* bp_module = nullptr;     // cudaLibrary_t of the specialised min-sum kernel
   void* bp_func = nullptr;       // its cudaKernel_t
   int bp_per_sm = 0;             // resident CTAs per SM
@@ -55,6 +58,10 @@ struct HostSide {
   std::vector<uint32_t> logicals;    // k*words_n (operators of the other type)
   std::vector<uint8_t> RA, RB;       // row factors: local checks = kron(RB, RA)
   int32_t kRA = 0, kRB = 0;
+  // Row grouping of the local code (per-qubit-prior posterior): F packs f_a = R_B x_a at bits
+  // a*kRB; empty when delta*kRB > 24 or R_B is rank-deficient.
+  std::vector<uint8_t> xcls;
+  std::vector<uint32_t> cbase, ckern;
   SideParams params{};
   std::vector<char> bp_cubin;        // specialised min-sum kernel (NVRTC output)
   int bp_block = 0, bp_spb = 0, bp_cluster = 1;

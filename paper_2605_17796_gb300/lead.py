@@ -79,6 +79,16 @@ EXPORTS = {
     "lead_decode_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_void_p,
                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "lead_priors_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts),
+                                                      ctypes.c_int64]),
+    "lead_local_estimate_priors": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_void_p,
+                                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                                  ctypes.c_void_p]),
+    "lead_decode_priors": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_void_p]),
     "lead_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lead_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -258,6 +268,27 @@ class Code:
         _check("lead_decode_noalloc", LIB.lead_decode_noalloc(self._h, ctypes.byref(opts), _ptr(syn), shots,
                                                               _ptr(corr), _ptr(status), _ptr(iters), _ptr(llr),
                                                               _stream(stream)))
+
+    def priors_workspace_bytes(self, opts: LeadDecodeOpts, shots: int) -> int:
+        return int(LIB.lead_priors_workspace_bytes(self._h, ctypes.byref(opts), shots))
+
+    def local_estimate_priors(self, opts: LeadDecodeOpts, syn, shots: int, prior, llr, q=None, ml=None,
+                              workspace=None, stream=None):
+        """lead_local_estimate_priors: Phases 1-2 with one prior probability per shot and qubit."""
+        ws = _ptr(workspace)
+        nb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        _check("lead_local_estimate_priors", LIB.lead_local_estimate_priors(
+            self._h, ctypes.byref(opts), _ptr(syn), shots, _ptr(prior), _ptr(llr), _ptr(q), _ptr(ml), ws, nb,
+            _stream(stream)))
+
+    def decode_priors(self, opts: LeadDecodeOpts, syn, shots: int, prior, corr, status, iters=None, llr=None,
+                      workspace=None, stream=None):
+        """lead_decode_priors: Algorithm 1 with one prior probability per shot and qubit."""
+        ws = _ptr(workspace)
+        nb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        _check("lead_decode_priors", LIB.lead_decode_priors(
+            self._h, ctypes.byref(opts), _ptr(syn), shots, _ptr(prior), _ptr(corr), _ptr(status), _ptr(iters),
+            _ptr(llr), ws, nb, _stream(stream)))
 
     def check(self, side: int, err, corr, shots: int, fail, stream=None):
         _check("lead_check", LIB.lead_check(self._h, side, _ptr(err), _ptr(corr), shots, _ptr(fail),
