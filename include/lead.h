@@ -61,6 +61,9 @@ extern "C" {
 
 /* precision modes of lead_decode_opts.precision */
 #define LEAD_PREC_FP32    0  /* binary32 priors and messages                                   */
+#define LEAD_PREC_BF16    1  /* LLRs stored as bfloat16 (round to nearest even), FP32 arithmetic  */
+#define LEAD_PREC_FP16    2  /* LLRs stored as IEEE binary16 (round to nearest even, saturating
+                                at +-65504), FP32 arithmetic                                    */
 
 typedef struct lead_code lead_code;   /* opaque; immutable after lead_build_code */
 
@@ -90,7 +93,7 @@ typedef struct {
   int32_t side;           /* 0 or 1                                                              */
   int32_t use_lead;       /* 1: Phases 1-3; 0: the standalone min-sum baseline on the channel prior */
   int32_t max_iter;       /* global min-sum iterations, 0..64                                    */
-  int32_t precision;      /* LEAD_PREC_FP32                                                       */
+  int32_t precision;      /* LEAD_PREC_*: storage format of the LLRs (see each entry point)       */
   float   alpha;          /* Phase-2 scaling, 0 < alpha <= 1 (Sec. III-B; 1 is the default)      */
   double  p;              /* channel marginal of this side's error type, 0 < p < 1/2              */
 } lead_decode_opts;
@@ -137,10 +140,13 @@ int lead_code_get_check_matrix(const lead_code* code, int32_t side, uint8_t* H);
  * lead_code_compile -- specialise the global min-sum kernel to this code (host only, no device
  * needed): the kernel source is compiled at run time (NVRTC, sm_103a) with the code's local
  * check supports as constants, so every loop over a check's support has a fixed trip count.
- * lead_code_prepare calls it when it has not run yet; calling it first moves the compile time
- * (about a second per side) out of the device set-up. log (host, nullable) receives the
- * compiler log, truncated to log_bytes. Errors: LEAD_EINVAL (sizes the kernel cannot serve),
- * LEAD_ECUDA (compilation failed; see the log).
+ * Compiles the kernels of both sides in every precision mode. lead_code_prepare compiles the
+ * binary32 kernels when they are missing, and a decode call in a 16-bit mode compiles and loads
+ * that mode's kernel on its first use; calling lead_code_compile first moves that compile time
+ * (about a second per kernel) out of the device set-up and out of the first decode call (which
+ * then only loads the module; make that first call outside stream capture). log (host,
+ * nullable) receives the compiler log, truncated to log_bytes. Errors: LEAD_EINVAL (sizes the
+ * kernel cannot serve), LEAD_ECUDA (compilation failed; see the log).
  */
 int lead_code_compile(lead_code* code, char* log, size_t log_bytes);
 
@@ -197,13 +203,16 @@ int lead_local_table(const lead_code* code, int32_t side, double p, float* table
 /*
  * lead_local_estimate -- Phases 1 and 2 (Algorithm 1): for every qubit i with views (v0, j0)
  * and (v1, j1) on the side, p_i = alpha * ((q(s_v0, j0) + q(s_v1, j1)) * 1/2) in binary32,
- * clamped to [2^-23, 1 - 2^-23], and llr[shot * n + i] = ln((1 - p_i)/p_i) (binary32; the
- * logarithm by the inverse-hyperbolic-tangent series, see the decode notes).
- *  syn (dev, shots x words_m[side]); llr (dev, shots x n float);
+ * clamped to [2^-23, 1 - 2^-23], and llr[shot * n + i] = ln((1 - p_i)/p_i) in binary32 (by
+ * linear interpolation in a 2817-node table over the binary32 exponent and top 7 fraction bits
+ * of min(p, 1-p), error below 1e-5), then stored in the format of opts->precision:
+ *   LEAD_PREC_FP32 float; LEAD_PREC_BF16 / LEAD_PREC_FP16 the 16-bit pattern (uint16) of the
+ *   bfloat16 / binary16 rounding (to nearest even) of that binary32 value.
+ *  syn (dev, shots x words_m[side]); llr (dev, shots x n elements of that format);
  *  workspace (dev) >= lead_workspace_bytes(opts), contents need not be initialised.
  */
 int lead_local_estimate(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn,
-                        int64_t shots, float* llr, void* workspace, size_t ws_bytes,
+                        int64_t shots, void* llr, void* workspace, size_t ws_bytes,
                         void* stream);
 
 /*
@@ -216,14 +225,19 @@ int lead_local_estimate(const lead_code* code, const lead_decode_opts* opts, con
  *         already satisfied the syndrome).
  *  llr    (dev, shots x n float, nullable) final posterior LLRs.
  *  Global min-sum (the paper's global decoder uses BP with min-sum; OSD is not included):
- *  flooding schedule, scaling 1, binary32 messages; c2v = (-1)^(s_c + #negative other v2c) *
- *  min |other v2c|, v2c = post - c2v, post_i = (lambda_i + U_v0) + U_v1 with U_v the sum of the
- *  messages from v's local rows in increasing row order (v0 < v1 the two views of qubit i),
- *  hard decision e_i = [post_i < 0], stop at the first iteration whose decision satisfies
- *  H e = s (iteration 0 tests the prior's decision).
+ *  flooding schedule, scaling 1, binary32 arithmetic; c2v = (-1)^(s_c + #negative other v2c) *
+ *  min |other v2c|, v2c = post - c2v (its sign is the IEEE sign bit), post_i = (lambda_i + U_v0)
+ *  + U_v1 with U_v the sum of the messages from v's local rows in increasing row order (v0 < v1
+ *  the two views of qubit i), hard decision e_i = [post_i < 0], stop at the first iteration
+ *  whose decision satisfies H e = s (iteration 0 tests the prior's decision).
+ *  opts->precision = LEAD_PREC_BF16 / LEAD_PREC_FP16 stores lambda_i, the c2v magnitudes (sign
+ *  applied after rounding), each U_v (summed in binary32, rounded once) and post_i rounded to
+ *  nearest even in that format; the hard decision reads the stored posterior. The first call
+ *  in a 16-bit mode compiles (unless lead_code_compile ran) and loads that mode's kernel.
  * shots == 0 is a no-op (pointers may then be NULL).
- * Errors: LEAD_EINVAL (including max_iter > 64 or alpha outside (0,1]; codes whose vertex count
- *        times the shared memory of one shot exceed one CTA), LEAD_ESTATE, LEAD_ECUDA.
+ * Errors: LEAD_EINVAL (including max_iter > 64, alpha outside (0,1] or an unknown precision;
+ *        codes whose vertex count times the shared memory of one shot exceed one CTA),
+ *        LEAD_ESTATE, LEAD_ECUDA.
  */
 int lead_decode(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn,
                 int64_t shots, uint32_t* corr, uint8_t* status, int32_t* iters, float* llr,
@@ -275,7 +289,9 @@ size_t lead_priors_workspace_bytes(const lead_code* code, const lead_decode_opts
 
 /*
  * lead_local_estimate_priors -- Phases 1-2 with per-qubit priors.
- *  llr    (dev, shots x n float) merged prior LLRs of the global decoder.
+ *  llr    (dev, shots x n float) merged prior LLRs of the global decoder, binary32 in every
+ *         precision mode (lead_decode_priors rounds them to the mode's format when it stores
+ *         them).
  *  q_out  (dev, shots x |G| x Delta^2 float, nullable) boosted local posteriors per view
  *         ([shot][vertex][j]); when NULL, the workspace holds them one pass at a time.
  *  ml_out (dev, shots x |G| uint64, nullable) the least-cost local decision of every view

@@ -29,6 +29,16 @@ Two numeric tracks:
   message update; the first t with H e = s stops (status bit 0); otherwise status bit 1 and the
   last decision is returned.
 
+Storage precision (a serving extension; the paper uses one precision): in the bfloat16 and
+binary16 modes every LLR the decoder keeps between steps is rounded to nearest even into that
+format when stored -- the prior lambda_i, the check-to-qubit magnitudes (the sign is applied
+after rounding), each per-view sum U_{v,j} (accumulated in binary32, rounded once), and the
+posterior post_i; arithmetic stays binary32 and the hard decision reads the stored posterior.
+Binary16 storage saturates at +-65504 (min-sum magnitudes can outgrow its range over many
+iterations; an infinity would turn later differences into NaN). The sign of a v2c message is
+its IEEE sign bit (a zero difference is +0 in binary32, but a
+binary16 posterior can underflow to -0).
+
 Parity: phases 1-2 are pinned through ``local``; the merge by the Appendix-A worked example;
 min-sum by its textbook special cases (exact ML on a cycle-free check matrix, zero syndrome
 -> zero correction at iteration 0, every converged output satisfies H e = s). Beyond those,
@@ -43,6 +53,28 @@ from .tanner import TannerCode
 
 STATUS_CONVERGED = 1
 STATUS_MAX_ITER = 2
+PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
+
+
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """binary32 -> nearest bfloat16 (ties to even) -> binary32: keep the top 16 bits of the
+    binary32 pattern after adding half an ulp of the kept part (plus one when the kept part is
+    odd). Finite inputs."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def round_storage(x: np.ndarray, precision: int) -> np.ndarray:
+    """The stored value of binary32 x in a precision mode, as binary32."""
+    x = np.asarray(x, dtype=np.float32)
+    if precision == PREC_FP32:
+        return x
+    if precision == PREC_BF16:
+        return round_bf16(x)
+    if precision == PREC_FP16:       # saturating at the largest finite binary16
+        return np.clip(x, np.float32(-65504.0), np.float32(65504.0)).astype(np.float16).astype(np.float32)
+    raise ValueError(precision)
 
 
 def local_syndromes(side: Side, syn: np.ndarray) -> np.ndarray:
@@ -164,16 +196,18 @@ def _syndrome_of(H: np.ndarray, e: np.ndarray) -> np.ndarray:
 
 
 def min_sum(H: np.ndarray, block: int, syn: np.ndarray, llr: np.ndarray, max_iter: int = 32,
-            early_stop: bool = True):
+            early_stop: bool = True, precision: int = PREC_FP32):
     """Phase 3, flooding min-sum in binary32 on the check matrix H whose rows come in blocks of
     ``block`` (one block per vertex view; the order of additions is documented in the module
     doc). syn (S, m) 0/1, llr (S, n) float32 -> (corr (S, n) uint8, status (S,) uint8,
     iters (S,) int32, post (S, n) float32 final posterior LLRs).
     ``early_stop=False`` runs all ``max_iter`` iterations and reports the last decision (used to
-    pin the message rules against the fixed point on cycle-free graphs)."""
+    pin the message rules against the fixed point on cycle-free graphs). ``precision`` selects
+    the storage format of the module doc."""
+    R = lambda x: round_storage(x, precision)  # noqa: E731
     g = _Graph(H, block)
     S, n = llr.shape
-    lam = llr.astype(np.float32)
+    lam = R(llr.astype(np.float32))
     corr = np.zeros((S, n), dtype=np.uint8)
     status = np.zeros(S, dtype=np.uint8)
     iters = np.zeros(S, dtype=np.int32)
@@ -191,13 +225,13 @@ def min_sum(H: np.ndarray, block: int, syn: np.ndarray, llr: np.ndarray, max_ite
             pa = post[active]
             v2c = (pa[:, g.nbr] - c2v[active]).astype(np.float32)
             mag = np.where(g.valid[None], np.abs(v2c), np.float32(np.inf)).astype(np.float32)
-            neg = (v2c < 0) & g.valid[None]
+            neg = np.signbit(v2c) & g.valid[None]
             # min over the other slots of a check = min(prefix minimum before k, suffix after k)
             inf = np.full(mag.shape[:2] + (1,), np.inf, dtype=np.float32)
             pre = np.concatenate([inf, np.minimum.accumulate(mag, axis=2)[:, :, :-1]], axis=2)
             suf = np.concatenate([np.minimum.accumulate(mag[:, :, ::-1], axis=2)[:, :, ::-1][:, :, 1:],
                                   inf], axis=2)
-            mn = np.minimum(pre, suf)
+            mn = R(np.minimum(pre, suf))
             # parity of the other slots' signs = parity of all of them XOR the slot's own sign
             par = ((neg.sum(axis=2) & 1).astype(bool)[:, :, None] ^ neg) ^ sgn_s[active][:, :, None]
             new = np.where(par, -mn, mn).astype(np.float32)
@@ -213,8 +247,8 @@ def min_sum(H: np.ndarray, block: int, syn: np.ndarray, llr: np.ndarray, max_ite
                     vals = np.where(ok[None], flat[:, edge_ix[:, tb, u]], np.float32(0.0))
                     U = (U + vals).astype(np.float32)
                 has = edge_ok[:, tb, 0]
-                acc = np.where(has[None], (acc + U).astype(np.float32), acc).astype(np.float32)
-            post[active] = acc
+                acc = np.where(has[None], (acc + R(U)).astype(np.float32), acc).astype(np.float32)
+            post[active] = R(acc)
         e = (post[active] < 0).astype(np.uint8)
         ok = (_syndrome_of(g.H, e) == syn[active]).all(axis=1)
         if not early_stop and t < max_iter:
@@ -237,14 +271,14 @@ def min_sum(H: np.ndarray, block: int, syn: np.ndarray, llr: np.ndarray, max_ite
 
 
 def decode(code: TannerCode, side_id: int, syn: np.ndarray, p: float, alpha: float = 1.0,
-           max_iter: int = 32, use_lead: bool = True):
+           max_iter: int = 32, use_lead: bool = True, precision: int = PREC_FP32):
     """Algorithm 1 on one side (use_lead=False: the standalone min-sum baseline)."""
     if use_lead:
         lam = prior_f32(code, side_id, syn, p, alpha)
     else:
         lam = channel_prior_f32(code.n, syn.shape[0], p)
     side = code.sides[side_id]
-    return min_sum(side.H, side.m_l, syn, lam, max_iter)
+    return min_sum(side.H, side.m_l, syn, lam, max_iter, precision=precision)
 
 
 def check(code: TannerCode, side_id: int, err: np.ndarray, corr: np.ndarray) -> np.ndarray:

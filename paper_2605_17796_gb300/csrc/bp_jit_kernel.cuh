@@ -1,9 +1,11 @@
 // Global min-sum decoder (Phase 3 of Algorithm 1, with Phases 1-2 fused into its prologue),
 // specialised at run time (NVRTC) to one code side. The generated prelude defines
 //   LEAD_NL (Delta^2), LEAD_ML (local rows m_l), LEAD_TS (threads with work = shots per CTA *
-//   |G|), LEAD_BLOCK (block size), LEAD_MINBLOCKS (CTAs per SM), LEAD_KMAX, and the
-//   constant tables lead_jit::kLen[ML] (row weights), kSupp[ML][KMAX] (local indices of every
-//   local row, increasing) and kRowMask[ML] (the same rows as 64-bit masks),
+//   |G|), LEAD_BLOCK (block size), LEAD_MINBLOCKS (CTAs per SM), LEAD_KMAX, LEAD_JMAX,
+//   LEAD_PREC (storage format), and the constant tables lead_jit::kLen[ML] (row weights),
+//   kSupp[ML][KMAX] (local indices of every local row, increasing), kRowMask[ML] (the same rows
+//   as 64-bit masks) and, per slot j, kJLen[NL], kJRow[NL][JMAX], kJPos[NL][JMAX] (the local
+//   rows touching j in increasing order and j's position in each row's support),
 // so every loop over a check's support below has compile-time trip counts and offsets.
 //
 // Mapping: one CTA handles `spb` shots; thread t = shot sl * |G| + vertex v. Shared memory is
@@ -22,6 +24,71 @@
 //   increasing local row order; v2c = post - c2v_old; hard decision e_i = [post_i < 0];
 //   iteration t tests H e = s first and stops at the first success (t = 0 tests the prior).
 
+namespace lead_jit {
+// Storage format of every LLR the decoder keeps between steps (LEAD_PREC: 0 binary32, 1 bfloat16,
+// 2 binary16): the prior, the check-to-variable magnitudes, the per-vertex sums U and the
+// posteriors. Arithmetic is binary32; a value is rounded to nearest even when stored (binary16
+// saturates at +-65504: min-sum magnitudes can grow past its range over many iterations).
+#if LEAD_PREC == 0
+typedef float msg_t;
+__device__ __forceinline__ msg_t enc(float v) { return v; }
+__device__ __forceinline__ float dec(msg_t h) { return h; }
+#else
+typedef unsigned short msg_t;
+__device__ __forceinline__ msg_t enc(float v) {
+  unsigned short h;
+#if LEAD_PREC == 1
+  asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(v));
+#else
+  // saturating: magnitudes beyond the largest finite binary16 (65504) are stored as 65504
+  v = fminf(fmaxf(v, -65504.0f), 65504.0f);
+  asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(v));
+#endif
+  return h;
+}
+__device__ __forceinline__ float dec(msg_t h) {
+#if LEAD_PREC == 1
+  return __uint_as_float((unsigned int)h << 16);
+#else
+  float f;
+  asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(h));
+  return f;
+#endif
+}
+#endif
+__device__ __forceinline__ float rnd(float v) { return dec(enc(v)); }
+
+// The two stored magnitudes (min1, min2) of a local row's compressed state: two binary32
+// registers, or both 16-bit patterns packed in one register.
+struct RowMag {
+#if LEAD_PREC == 0
+  float a, b;
+  __device__ __forceinline__ float m1() const { return a; }
+  __device__ __forceinline__ float m2() const { return b; }
+  __device__ __forceinline__ void set(float n1, float n2) {
+    a = n1;
+    b = n2;
+  }
+#else
+  unsigned int w;
+  __device__ __forceinline__ float m1() const { return dec((msg_t)(w & 0xFFFFu)); }
+  __device__ __forceinline__ float m2() const { return dec((msg_t)(w >> 16)); }
+  __device__ __forceinline__ void set(float n1, float n2) { w = (unsigned int)enc(n1) | ((unsigned int)enc(n2) << 16); }
+#endif
+};
+
+// Shared-memory offset (bytes) of the word arrays behind the three NL x TS message arrays.
+constexpr unsigned int kMsgBytes = ((3u * LEAD_NL * LEAD_TS * (unsigned int)sizeof(msg_t)) + 15u) & ~15u;
+
+// New check-to-variable message of local row r to its k-th support position, from the row's
+// compressed state (m1, m2 magnitudes; meta = signs | argmin << 26 | parity << 31).
+__device__ __forceinline__ float c2v_msg(float m1, float m2, unsigned int meta, int k) {
+  const unsigned int flip = meta ^ (0u - (meta >> 31));   // bit k: sign of the message to k
+  const float mag = (k == (int)((meta >> 26) & 31u)) ? m2 : m1;
+  return __uint_as_float(__float_as_uint(mag) ^ (((flip >> k) & 1u) << 31));
+}
+}  // namespace lead_jit
+
 #if LEAD_CLUSTER == 1
 namespace lead_jit {
 
@@ -30,10 +97,10 @@ lead_bp_jit(const lead::BPJitArgs a) {
   constexpr int NL = LEAD_NL, ML = LEAD_ML, TS = LEAD_TS;
   extern __shared__ __align__(16) unsigned int smem[];
   const int V = a.order, spb = a.spb, wm = a.words_m;
-  float* Us = reinterpret_cast<float*>(smem);
-  float* Ps = Us + NL * TS;
-  float* Ls = Ps + NL * TS;
-  unsigned int* syn_s = reinterpret_cast<unsigned int*>(Ls + NL * TS);
+  msg_t* Us = reinterpret_cast<msg_t*>(smem);
+  msg_t* Ps = Us + NL * TS;
+  msg_t* Ls = Ps + NL * TS;
+  unsigned int* syn_s = smem + kMsgBytes / 4;
   unsigned int* cb = syn_s + spb * wm;
   int* flags = reinterpret_cast<int*>(cb + spb * a.words_n);
   const unsigned short* __restrict__ PA = a.pa;
@@ -50,12 +117,11 @@ lead_bp_jit(const lead::BPJitArgs a) {
     if (tid < 2 * spb) flags[tid] = 0;
     __syncthreads();
     const bool act = lane_ok && sl < nsh;
-    float m1[ML], m2[ML];
+    RowMag mag[ML];
     unsigned int meta[ML];
 #pragma unroll
     for (int r = 0; r < ML; ++r) {
-      m1[r] = 0.0f;
-      m2[r] = 0.0f;
+      mag[r].set(0.0f, 0.0f);
       meta[r] = 0u;
     }
     unsigned int sv = 0;
@@ -64,18 +130,20 @@ lead_bp_jit(const lead::BPJitArgs a) {
       sv = lead::bit_field(srow, v * ML, ML);
 #pragma unroll 2
       for (int j = 0; j < NL; ++j) {
+        float lj;
         if (a.lam) {
-          Ls[j * TS + tid] = __ldg(a.lam + (g0 + sl) * a.n + __ldg(a.views + v * NL + j));
+          lj = __ldg(a.lam + (g0 + sl) * a.n + __ldg(a.views + v * NL + j));
         } else if (a.use_lead) {
           const unsigned int addr = __ldg(PA + j * TS + tid) & 0x7FFFu;
           const unsigned int jp = addr / TS, vp = addr - jp * TS - sl * V;
           const unsigned int svp = lead::bit_field(srow, vp * ML, ML);
-          Ls[j * TS + tid] = lead::merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp),
-                                              a.alpha, a.llr_t0, a.llr_t1);
+          lj = lead::merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp), a.alpha, a.llr_t0,
+                                a.llr_t1);
         } else {
-          Ls[j * TS + tid] = lam_ch;
+          lj = lam_ch;
         }
-        Us[j * TS + tid] = 0.0f;
+        Ls[j * TS + tid] = enc(lj);
+        Us[j * TS + tid] = enc(0.0f);
       }
     }
     __syncthreads();
@@ -87,12 +155,12 @@ lead_bp_jit(const lead::BPJitArgs a) {
 #pragma unroll
         for (int j = 0; j < NL; ++j) {
           const unsigned int pa = __ldg(PA + j * TS + tid);
-          const float up = Us[pa & 0x7FFFu];
-          const float uo = Us[j * TS + tid];
-          const float lj = Ls[j * TS + tid];
-          const float pj = (pa >> 15) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo);
-          Ps[j * TS + tid] = pj;
-          hm |= (unsigned long long)(pj < 0.0f) << j;
+          const float up = dec(Us[pa & 0x7FFFu]);
+          const float uo = dec(Us[j * TS + tid]);
+          const float lj = dec(Ls[j * TS + tid]);
+          const msg_t pe = enc((pa >> 15) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo));
+          Ps[j * TS + tid] = pe;
+          hm |= (unsigned long long)(dec(pe) < 0.0f) << j;
         }
 #pragma unroll
         for (int r = 0; r < ML; ++r) bad |= (unsigned int)(__popcll(hm & kRowMask[r]) ^ (sv >> r)) & 1u;
@@ -113,7 +181,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
           if (__ldg(PA + j * TS + tid) >> 15) {
             const int q = __ldg(a.views + v * NL + j);
             if ((hm >> j) & 1) atomicOr(cb + sl * a.words_n + (q >> 5), 1u << (q & 31));
-            if (a.llr) a.llr[shot * a.n + q] = Ps[j * TS + tid];
+            if (a.llr) a.llr[shot * a.n + q] = dec(Ps[j * TS + tid]);
           }
         }
         if (v == 0) {
@@ -130,7 +198,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
       if (!mydone) {
 #pragma unroll
         for (int r = 0; r < ML; ++r) {
-          const float m1o = m1[r], m2o = m2[r];
+          const float m1o = mag[r].m1(), m2o = mag[r].m2();
           const unsigned int mo = meta[r];
           const int amo = (int)((mo >> 26) & 31u);
           const unsigned int flip = mo ^ (0u - (mo >> 31));   // bit k: sign of the old message to k
@@ -142,7 +210,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
             if (k >= kLen[r]) break;      // constant after unrolling
             const float mago = (k == amo) ? m2o : m1o;
             const float co = __uint_as_float(__float_as_uint(mago) ^ ((flip >> k) << 31));
-            const float v2c = __fsub_rn(Ps[kSupp[r][k] * TS + tid], co);
+            const float v2c = __fsub_rn(dec(Ps[kSupp[r][k] * TS + tid]), co);
             const float m = fabsf(v2c);
             // v2c is never -0 (every sum starts from +0 terms): its sign bit equals v2c < 0
             sg |= (__float_as_uint(v2c) >> 31) << k;
@@ -152,19 +220,22 @@ lead_bp_jit(const lead::BPJitArgs a) {
             am = lt ? k : am;
           }
           const unsigned int par = ((unsigned int)__popc(sg) ^ (sv >> r)) & 1u;
-          m1[r] = n1;
-          m2[r] = n2;
+          mag[r].set(n1, n2);
           meta[r] = sg | ((unsigned int)am << 26) | (par << 31);
-          const unsigned int nflip = sg ^ (0u - par);    // bit k: sign of the new message to k
+        }
+        // U of every slot: its rows' new messages summed in increasing row order (binary32, the
+        // first term stored as is: 0 + c == c), then stored once
 #pragma unroll
-          for (int k = 0; k < LEAD_KMAX; ++k) {
-            if (k >= kLen[r]) break;      // constant after unrolling
-            const float mag = (k == am) ? n2 : n1;
-            const float c = __uint_as_float(__float_as_uint(mag) ^ ((nflip >> k) << 31));
-            float* u = Us + kSupp[r][k] * TS + tid;
-            // the first local row touching a slot stores, later rows add (0 + c == c exactly)
-            *u = kFirst[r][k] ? c : __fadd_rn(*u, c);
+        for (int j = 0; j < NL; ++j) {
+          float u = 0.0f;
+#pragma unroll
+          for (int i = 0; i < LEAD_JMAX; ++i) {
+            if (i >= kJLen[j]) break;     // constant after unrolling
+            const int r = kJRow[j][i];
+            const float c = c2v_msg(mag[r].m1(), mag[r].m2(), meta[r], kJPos[j][i]);
+            u = (i == 0) ? c : __fadd_rn(u, c);
           }
+          Us[j * TS + tid] = enc(u);
         }
       }
       __syncthreads();
@@ -212,6 +283,16 @@ __device__ __forceinline__ float ld_cluster_f32(unsigned int addr) {
   return v;
 }
 
+__device__ __forceinline__ msg_t ld_cluster_msg(unsigned int addr) {
+#if LEAD_PREC == 0
+  return ld_cluster_f32(addr);
+#else
+  unsigned short v;
+  asm volatile("ld.shared::cluster.u16 %0, [%1];" : "=h"(v) : "r"(addr) : "memory");
+  return v;
+#endif
+}
+
 __device__ __forceinline__ unsigned int ld_cluster_u32(unsigned int addr) {
   unsigned int v;
   asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
@@ -231,10 +312,10 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
   constexpr int NL = LEAD_NL, ML = LEAD_ML, TS = LEAD_TS, C = LEAD_CLUSTER;
   extern __shared__ __align__(16) unsigned int smem[];
   const int V = a.order, wm = a.words_m;
-  float* Us = reinterpret_cast<float*>(smem);
-  float* Ps = Us + NL * TS;
-  float* Ls = Ps + NL * TS;
-  unsigned int* syn_s = reinterpret_cast<unsigned int*>(Ls + NL * TS);
+  msg_t* Us = reinterpret_cast<msg_t*>(smem);
+  msg_t* Ps = Us + NL * TS;
+  msg_t* Ls = Ps + NL * TS;
+  unsigned int* syn_s = smem + kMsgBytes / 4;
   unsigned int* cb = syn_s + wm;
   unsigned int* flags = cb + a.words_n;          // two words, meaningful in rank 0 only
   const unsigned int* __restrict__ PA = reinterpret_cast<const unsigned int*>(a.pa);
@@ -254,12 +335,11 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
     for (int i = tid; i < wm; i += blockDim.x) syn_s[i] = __ldg(a.syn + g0 * wm + i);
     for (int i = tid; i < a.words_n; i += blockDim.x) cb[i] = 0u;
     if (tid < 2) flags[tid] = 0u;
-    float m1[ML], m2[ML];
+    RowMag mag[ML];
     unsigned int meta[ML];
 #pragma unroll
     for (int r = 0; r < ML; ++r) {
-      m1[r] = 0.0f;
-      m2[r] = 0.0f;
+      mag[r].set(0.0f, 0.0f);
       meta[r] = 0u;
     }
     __syncthreads();
@@ -268,19 +348,21 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
       sv = lead::bit_field(syn_s, v * ML, ML);
 #pragma unroll 2
       for (int j = 0; j < NL; ++j) {
+        float lj;
         if (a.lam) {
-          Ls[j * TS + tid] = __ldg(a.lam + g0 * a.n + __ldg(a.views + v * NL + j));
+          lj = __ldg(a.lam + g0 * a.n + __ldg(a.views + v * NL + j));
         } else if (a.use_lead) {
           const unsigned int pa = __ldg(PA + j * V + v);
           const unsigned int addr = pa & 0xFFFFu, pr = (pa >> 16) & 0xFFu;
           const unsigned int jp = addr / TS, vp = pr * TS + (addr - jp * TS);
           const unsigned int svp = lead::bit_field(syn_s, vp * ML, ML);
-          Ls[j * TS + tid] = lead::merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp),
-                                              a.alpha, a.llr_t0, a.llr_t1);
+          lj = lead::merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp), a.alpha, a.llr_t0,
+                                a.llr_t1);
         } else {
-          Ls[j * TS + tid] = lam_ch;
+          lj = lam_ch;
         }
-        Us[j * TS + tid] = 0.0f;
+        Ls[j * TS + tid] = enc(lj);
+        Us[j * TS + tid] = enc(0.0f);
       }
     }
     cluster_sync();             // zeroed U and cleared flags visible to the whole cluster
@@ -295,12 +377,12 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
           unsigned int ub = ubase[0];
 #pragma unroll
           for (int r = 1; r < C; ++r) ub = (pr == (unsigned int)r) ? ubase[r] : ub;
-          const float up = (pr == rank) ? Us[addr] : ld_cluster_f32(ub + 4u * addr);
-          const float uo = Us[j * TS + tid];
-          const float lj = Ls[j * TS + tid];
-          const float pj = (pa >> 31) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo);
-          Ps[j * TS + tid] = pj;
-          hm |= (unsigned long long)(pj < 0.0f) << j;
+          const float up = dec((pr == rank) ? Us[addr] : ld_cluster_msg(ub + (unsigned int)sizeof(msg_t) * addr));
+          const float uo = dec(Us[j * TS + tid]);
+          const float lj = dec(Ls[j * TS + tid]);
+          const msg_t pe = enc((pa >> 31) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo));
+          Ps[j * TS + tid] = pe;
+          hm |= (unsigned long long)(dec(pe) < 0.0f) << j;
         }
 #pragma unroll
         for (int r = 0; r < ML; ++r) bad |= (unsigned int)(__popcll(hm & kRowMask[r]) ^ (sv >> r)) & 1u;
@@ -315,7 +397,7 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
             if (__ldg(PA + j * V + v) >> 31) {
               const int q = __ldg(a.views + v * NL + j);
               if ((hm >> j) & 1) atomicOr(cb + (q >> 5), 1u << (q & 31));
-              if (a.llr) a.llr[g0 * a.n + q] = Ps[j * TS + tid];
+              if (a.llr) a.llr[g0 * a.n + q] = dec(Ps[j * TS + tid]);
             }
           }
         }
@@ -328,7 +410,7 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
       if (lane_ok) {
 #pragma unroll
         for (int r = 0; r < ML; ++r) {
-          const float m1o = m1[r], m2o = m2[r];
+          const float m1o = mag[r].m1(), m2o = mag[r].m2();
           const unsigned int mo = meta[r];
           const int amo = (int)((mo >> 26) & 31u);
           const unsigned int flip = mo ^ (0u - (mo >> 31));
@@ -340,7 +422,7 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
             if (k >= kLen[r]) break;
             const float mago = (k == amo) ? m2o : m1o;
             const float co = __uint_as_float(__float_as_uint(mago) ^ ((flip >> k) << 31));
-            const float v2c = __fsub_rn(Ps[kSupp[r][k] * TS + tid], co);
+            const float v2c = __fsub_rn(dec(Ps[kSupp[r][k] * TS + tid]), co);
             const float m = fabsf(v2c);
             sg |= (__float_as_uint(v2c) >> 31) << k;
             const bool lt = m < n1;
@@ -349,18 +431,22 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
             am = lt ? k : am;
           }
           const unsigned int par = ((unsigned int)__popc(sg) ^ (sv >> r)) & 1u;
-          m1[r] = n1;
-          m2[r] = n2;
+          mag[r].set(n1, n2);
           meta[r] = sg | ((unsigned int)am << 26) | (par << 31);
-          const unsigned int nflip = sg ^ (0u - par);
+        }
+        // U of every slot: its rows' new messages summed in increasing row order (binary32, the
+        // first term stored as is: 0 + c == c), then stored once
 #pragma unroll
-          for (int k = 0; k < LEAD_KMAX; ++k) {
-            if (k >= kLen[r]) break;
-            const float mag = (k == am) ? n2 : n1;
-            const float c = __uint_as_float(__float_as_uint(mag) ^ ((nflip >> k) << 31));
-            float* u = Us + kSupp[r][k] * TS + tid;
-            *u = kFirst[r][k] ? c : __fadd_rn(*u, c);
+        for (int j = 0; j < NL; ++j) {
+          float u = 0.0f;
+#pragma unroll
+          for (int i = 0; i < LEAD_JMAX; ++i) {
+            if (i >= kJLen[j]) break;     // constant after unrolling
+            const int r = kJRow[j][i];
+            const float c = c2v_msg(mag[r].m1(), mag[r].m2(), meta[r], kJPos[j][i]);
+            u = (i == 0) ? c : __fadd_rn(u, c);
           }
+          Us[j * TS + tid] = enc(u);
         }
       }
       cluster_sync();           // every CTA's U complete before the next gather

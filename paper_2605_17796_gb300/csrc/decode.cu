@@ -1,8 +1,11 @@
 // Phases 1-2 (local estimation + regularised merge) and Phase 3 (global min-sum with a
 // bit-packed syndrome check per iteration) of Algorithm 1.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "bp_jit_args.h"
 #include "lead_device.cuh"
@@ -25,15 +28,27 @@ struct LocalArgs {
   const uint32_t* qslots;
   const float* llr_t0;
   const float* llr_t1;
-  float* llr;
+  void* llr;                    // float, or the 16-bit pattern of the storage format
 };
+
+// Store an LLR in the precision mode's storage format (round to nearest even).
+template <int PREC>
+__device__ __forceinline__ void store_llr(void* base, int64_t idx, float v) {
+  if constexpr (PREC == LEAD_PREC_BF16)
+    __stcs(static_cast<unsigned short*>(base) + idx, __bfloat16_as_ushort(__float2bfloat16_rn(v)));
+  else if constexpr (PREC == LEAD_PREC_FP16)   // saturating at the largest finite binary16
+    __stcs(static_cast<unsigned short*>(base) + idx,
+           __half_as_ushort(__float2half_rn(fminf(fmaxf(v, -65504.0f), 65504.0f))));
+  else
+    __stcs(static_cast<float*>(base) + idx, v);
+}
 
 // Phases 1-2 for every (shot, qubit): per batch of shots, the local syndromes s_v of all
 // vertices are extracted once into shared memory; then every qubit reads its two views'
 // boosted local posteriors from the per-syndrome table (shared memory) and merges them into
 // the prior LLR. Each thread keeps its qubits' view coordinates in registers for the whole
 // persistent loop; the LLR rows are written with consecutive threads on consecutive qubits.
-template <int NL, int KQ>
+template <int NL, int KQ, int PREC>
 __global__ void __launch_bounds__(kLocalThreads, 2)
 local_estimate_kernel(LocalArgs a, __grid_constant__ const SideParams P) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -66,14 +81,14 @@ local_estimate_kernel(LocalArgs a, __grid_constant__ const SideParams P) {
 #pragma unroll 4
     for (int sl = 0; sl < nsh; ++sl) {
       const uint16_t* svr = sv_s + sl * V;
-      float* out = a.llr + (b0 + sl) * (int64_t)a.n;
+      const int64_t row = (b0 + sl) * (int64_t)a.n;
 #pragma unroll
       for (int k = 0; k < KQ; ++k) {
         const int i = threadIdx.x + k * kLocalThreads;
         if (i < a.n) {
           const float q0 = tab[svr[vv[k] & 0xFFFFu] * NL + (jj[k] & 0xFFFFu)];
           const float q1 = tab[svr[vv[k] >> 16] * NL + (jj[k] >> 16)];
-          __stcs(out + i, merged_llr_s(q0, q1, a.alpha, tv));
+          store_llr<PREC>(a.llr, row + i, merged_llr_s(q0, q1, a.alpha, tv));
         }
       }
     }
@@ -98,7 +113,8 @@ int validate_opts(const lead_code* code, const lead_decode_opts* o) {
   if (o->max_iter < 0 || o->max_iter > kMaxIter) return LEAD_EINVAL;
   if (!(o->alpha > 0.0f && o->alpha <= 1.0f)) return LEAD_EINVAL;
   if (!(o->p > 0.0 && o->p < 0.5)) return LEAD_EINVAL;
-  if (o->precision != LEAD_PREC_FP32) return LEAD_EINVAL;
+  if (o->precision != LEAD_PREC_FP32 && o->precision != LEAD_PREC_BF16 && o->precision != LEAD_PREC_FP16)
+    return LEAD_EINVAL;
   if (code->nl != 16 && code->nl != 36) return LEAD_EINVAL;
   return LEAD_OK;
 }
@@ -110,9 +126,9 @@ int set_smem(K kernel, size_t bytes) {
   return LEAD_OK;
 }
 
-template <int NL>
+template <int NL, int PREC>
 int launch_local(const lead_code* code, const lead_decode_opts* o, const uint32_t* syn, int64_t shots,
-                 float* llr, const float* table, cudaStream_t stream) {
+                 void* llr, const float* table, cudaStream_t stream) {
   const SideParams& P = code->side[o->side].params;
   LocalArgs a{};
   a.n = code->n;
@@ -140,10 +156,10 @@ int launch_local(const lead_code* code, const lead_decode_opts* o, const uint32_
     LEAD_CUDA_TRY(cudaGetLastError());
     return LEAD_OK;
   };
-  if (kq <= 1) return pick(local_estimate_kernel<NL, 1>);
-  if (kq <= 2) return pick(local_estimate_kernel<NL, 2>);
-  if (kq <= 6) return pick(local_estimate_kernel<NL, 6>);
-  if (kq <= 24) return pick(local_estimate_kernel<NL, 24>);
+  if (kq <= 1) return pick(local_estimate_kernel<NL, 1, PREC>);
+  if (kq <= 2) return pick(local_estimate_kernel<NL, 2, PREC>);
+  if (kq <= 6) return pick(local_estimate_kernel<NL, 6, PREC>);
+  if (kq <= 24) return pick(local_estimate_kernel<NL, 24, PREC>);
   return LEAD_EINVAL;
 }
 
@@ -177,7 +193,7 @@ int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* 
   a.llr_t0 = code->d_llr;
   a.llr_t1 = code->d_llr + kLlrNodes;
   if (!a.pa) return LEAD_EINVAL;
-  return jit_launch_bp(code, o->side, a, sm_count(code->device), stream);
+  return jit_launch_bp(code, o->side, o->precision, a, sm_count(code->device), stream);
 }
 
 }  // namespace lead
@@ -191,7 +207,7 @@ size_t lead_workspace_bytes(const lead_code* code, const lead_decode_opts* opts,
 }
 
 int lead_local_estimate(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn,
-                        int64_t shots, float* llr, void* workspace, size_t ws_bytes, void* stream) {
+                        int64_t shots, void* llr, void* workspace, size_t ws_bytes, void* stream) {
   using namespace lead;
   int rc = check_device(code);
   if (rc != LEAD_OK) return rc;
@@ -205,8 +221,14 @@ int lead_local_estimate(const lead_code* code, const lead_decode_opts* opts, con
   float* table = static_cast<float*>(workspace);
   rc = launch_table(code, opts->side, opts->p, table, s);
   if (rc != LEAD_OK) return rc;
-  if (code->nl == 16) return launch_local<16>(code, opts, syn, shots, llr, table, s);
-  return launch_local<36>(code, opts, syn, shots, llr, table, s);
+  auto go = [&](auto prec) -> int {
+    constexpr int PR = decltype(prec)::value;
+    if (code->nl == 16) return launch_local<16, PR>(code, opts, syn, shots, llr, table, s);
+    return launch_local<36, PR>(code, opts, syn, shots, llr, table, s);
+  };
+  if (opts->precision == LEAD_PREC_BF16) return go(std::integral_constant<int, LEAD_PREC_BF16>{});
+  if (opts->precision == LEAD_PREC_FP16) return go(std::integral_constant<int, LEAD_PREC_FP16>{});
+  return go(std::integral_constant<int, LEAD_PREC_FP32>{});
 }
 
 int lead_decode(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn,

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -25,25 +26,31 @@ namespace {
 
 }  // namespace
 
-Geometry bp_geometry(const lead_code* code, int side) {
+// Bytes of one stored LLR in a precision mode.
+static size_t msg_bytes(int prec) { return prec == LEAD_PREC_FP32 ? 4 : 2; }
+
+Geometry bp_geometry(const lead_code* code, int side, int prec) {
   const SideParams& P = code->side[side].params;
   Geometry g{};
-  auto smem_for = [&](int ts, int spb) {
-    return sizeof(uint32_t) * ((size_t)ts * code->nl * 3 + (size_t)spb * P.words_m + (size_t)spb * code->words_n +
-                               2 * (size_t)spb);
+  auto smem_for = [&](int ts, int spb, size_t mb) {
+    const size_t msgs = ((size_t)ts * code->nl * 3 * mb + 15) & ~size_t(15);
+    return msgs + sizeof(uint32_t) * ((size_t)spb * P.words_m + (size_t)spb * code->words_n + 2 * (size_t)spb);
   };
+  // The split of shots and vertices over CTAs is fixed by the binary32 footprint, so every
+  // precision mode shares one partner table; the 16-bit modes only need less shared memory.
   g.spb = bp_shots_per_block(code);
   g.cluster = 1;
   g.ts = g.spb * code->order;
-  g.smem = smem_for(g.ts, g.spb);
+  size_t smem32 = smem_for(g.ts, g.spb, 4);
   // a shot whose state does not leave room for two CTAs per SM is split over a thread-block
   // cluster (distributed shared memory), 2, 4 or 8 CTAs
-  while (g.smem > 120u * 1024u && g.cluster < 8) {
+  while (smem32 > 120u * 1024u && g.cluster < 8) {
     g.cluster *= 2;
     g.spb = 1;
     g.ts = (code->order + g.cluster - 1) / g.cluster;
-    g.smem = smem_for(g.ts, 1);
+    smem32 = smem_for(g.ts, 1, 4);
   }
+  g.smem = smem_for(g.ts, g.spb, msg_bytes(prec));
   g.block = (g.ts + 31) / 32 * 32;
   // CTAs per SM that shared memory allows (227 KB usable, 1 KB reserved per CTA), capped so
   // that each thread keeps at least 64 registers
@@ -55,7 +62,7 @@ Geometry bp_geometry(const lead_code* code, int side) {
 
 namespace {
 
-std::string prelude(const lead_code* code, int side, const Geometry& g) {
+std::string prelude(const lead_code* code, int side, const Geometry& g, int prec) {
   const SideParams& P = code->side[side].params;
   int kmax = 1;
   for (int r = 0; r < P.m_l; ++r) kmax = std::max(kmax, P.supp_len[r]);
@@ -68,6 +75,14 @@ std::string prelude(const lead_code* code, int side, const Geometry& g) {
     << "#define LEAD_KMAX " << kmax << "\n"
     << "#define LEAD_SPB " << g.spb << "\n"
     << "#define LEAD_CLUSTER " << g.cluster << "\n"
+    << "#define LEAD_PREC " << prec << "\n";
+  // the local rows touching every slot j (increasing) and j's position in each row's support
+  std::vector<std::vector<std::pair<int, int>>> rows_of(code->nl);
+  for (int r = 0; r < P.m_l; ++r)
+    for (int k = 0; k < P.supp_len[r]; ++k) rows_of[P.supp[r][k]].push_back({r, k});
+  int jmax = 1;
+  for (const auto& v : rows_of) jmax = std::max(jmax, (int)v.size());
+  s << "#define LEAD_JMAX " << jmax << "\n"
     << "namespace lead_jit {\n";
   s << "__device__ constexpr int kLen[" << P.m_l << "] = {";
   for (int r = 0; r < P.m_l; ++r) s << (r ? "," : "") << P.supp_len[r];
@@ -77,21 +92,18 @@ std::string prelude(const lead_code* code, int side, const Geometry& g) {
     for (int k = 0; k < kmax; ++k) s << (k ? "," : "") << (k < P.supp_len[r] ? (int)P.supp[r][k] : 0);
     s << "}";
   }
-  // kFirst[r][k]: row r is the first local row (in increasing order) that touches slot supp[r][k]
-  s << "};\n__device__ constexpr bool kFirst[" << P.m_l << "][" << kmax << "] = {";
-  for (int r = 0; r < P.m_l; ++r) {
-    s << (r ? ",{" : "{");
-    for (int k = 0; k < kmax; ++k) {
-      bool first = false;
-      if (k < P.supp_len[r]) {
-        const int j = P.supp[r][k];
-        first = true;
-        for (int r2 = 0; r2 < r; ++r2)
-          if ((P.rowmask[r2] >> j) & 1) first = false;
+  s << "};\n__device__ constexpr int kJLen[" << code->nl << "] = {";
+  for (int j = 0; j < code->nl; ++j) s << (j ? "," : "") << rows_of[j].size();
+  for (int part = 0; part < 2; ++part) {
+    s << "};\n__device__ constexpr int " << (part ? "kJPos" : "kJRow") << "[" << code->nl << "][" << jmax << "] = {";
+    for (int j = 0; j < code->nl; ++j) {
+      s << (j ? ",{" : "{");
+      for (int i = 0; i < jmax; ++i) {
+        const int val = i < (int)rows_of[j].size() ? (part ? rows_of[j][i].second : rows_of[j][i].first) : 0;
+        s << (i ? "," : "") << val;
       }
-      s << (k ? "," : "") << (first ? "true" : "false");
+      s << "}";
     }
-    s << "}";
   }
   s << "};\n__device__ constexpr unsigned long long kRowMask[" << P.m_l << "] = {";
   for (int r = 0; r < P.m_l; ++r) s << (r ? "," : "") << P.rowmask[r] << "ull";
@@ -101,99 +113,176 @@ std::string prelude(const lead_code* code, int side, const Geometry& g) {
 
 }  // namespace
 
+// NVRTC compile of the kernel for one side and precision mode into hs.bp_cubin[prec].
+namespace {
+
+// Sum of the "N bytes spill stores" figures in a ptxas -v report.
+long spill_bytes(const std::string& log) {
+  long total = 0;
+  const std::string key = " bytes spill stores";
+  for (size_t pos = log.find(key); pos != std::string::npos; pos = log.find(key, pos + 1)) {
+    size_t b = pos;
+    while (b > 0 && log[b - 1] >= '0' && log[b - 1] <= '9') --b;
+    if (b < pos) total += std::strtol(log.c_str() + b, nullptr, 10);
+  }
+  return total;
+}
+
+// One NVRTC compile; returns the cubin (empty on failure) and the compiler log.
+int nvrtc_build(const std::string& src, int maxreg, std::vector<char>* cubin, std::string* log) {
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "lead_bp_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+    return LEAD_ECUDA;
+  const std::string regopt = "--maxrregcount=" + std::to_string(maxreg);
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=false", "-lineinfo",
+                        regopt.c_str(), "--ptxas-options=-v"};
+  const nvrtcResult rc = nvrtcCompileProgram(prog, 6, opts);
+  size_t logn = 0;
+  nvrtcGetProgramLogSize(prog, &logn);
+  log->assign(logn, '\0');
+  if (logn) nvrtcGetProgramLog(prog, &(*log)[0]);
+  log->resize(std::strlen(log->c_str()));          // the reported size counts the terminating NUL
+  if (rc != NVRTC_SUCCESS) {
+    nvrtcDestroyProgram(&prog);
+    return LEAD_ECUDA;
+  }
+  size_t n = 0;
+  nvrtcGetCUBINSize(prog, &n);
+  cubin->resize(n);
+  nvrtcGetCUBIN(prog, cubin->data());
+  nvrtcDestroyProgram(&prog);
+  return LEAD_OK;
+}
+
+}  // namespace
+
+// Spill stores tolerated at a register cap: a few words, which stay in L1.
+constexpr long kSpillSlack = 16;
+
+// NVRTC compile of the kernel for one side and precision mode into hs.bp_cubin[prec]. The
+// resident CTAs per SM start at what shared memory allows and step down while the register
+// cap that occupancy implies makes the compiler spill more than kSpillSlack bytes.
+int compile_one(lead_code* code, int side, int prec, std::string* log_out) {
+  HostSide& hs = code->side[side];
+  if (!hs.bp_cubin[prec].empty()) return LEAD_OK;
+  Geometry g = bp_geometry(code, side, prec);
+  if (g.block > 1024 || (size_t)code->nl * g.ts >= 32768 || g.smem > 227u * 1024u) return LEAD_EINVAL;
+  // LEAD_JIT_PTXAS_VERBOSE=1 keeps the assembler's register / spill report in the log
+  const char* verbose = std::getenv("LEAD_JIT_PTXAS_VERBOSE");
+  std::vector<char> cubin;
+  std::string log;
+  int maxreg = 0;
+  std::ostringstream tries;
+  for (;; --g.minblocks) {
+    // registers per thread that let LEAD_MINBLOCKS CTAs of this size share an SM
+    maxreg = std::min(255, (65536 / (g.block * g.minblocks)) & ~7);
+    const std::string src = prelude(code, side, g, prec) + kLeadJitSource;
+    const int rc = nvrtc_build(src, maxreg, &cubin, &log);
+    if (rc != LEAD_OK) {
+      if (log_out) *log_out += log;
+      return rc;
+    }
+    const long spill = spill_bytes(log);
+    tries << "  " << g.minblocks << " CTA(s) per SM, <= " << maxreg << " registers: " << spill << " B spilled\n";
+    if (g.minblocks == 1 || spill <= kSpillSlack) break;
+  }
+  if (log_out) {
+    std::ostringstream gs;
+    gs << "side " << side << " precision " << prec << ": " << (g.cluster > 1 ? "cluster of " : "") << g.cluster
+       << " CTA(s) x " << g.block << " threads, " << g.ts << " slots per CTA row, " << g.spb
+       << " shot(s) per CTA, " << g.smem << " B shared memory, " << g.minblocks << " CTA(s) per SM, <= " << maxreg
+       << " registers\n";
+    *log_out += gs.str() + tries.str();
+    if (verbose && verbose[0] == '1') *log_out += log;
+  }
+  hs.bp_cubin[prec] = std::move(cubin);
+  hs.bp_block = g.block;
+  hs.bp_spb = g.spb;
+  hs.bp_cluster = g.cluster;
+  hs.bp_smem[prec] = g.smem;
+  return LEAD_OK;
+}
+
+namespace {
+
+// Loads the compiled kernel of (side, prec) on the current device.
+int load_one(lead_code* code, int side, int prec) {
+  HostSide& hs = code->side[side];
+  DeviceSide& ds = code->dside[side];
+  if (ds.bp_func[prec]) return LEAD_OK;
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kern = nullptr;
+  if (cudaLibraryLoadData(&lib, hs.bp_cubin[prec].data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess)
+    return LEAD_ECUDA;
+  int per_sm = 0;
+  const char* name = hs.bp_cluster > 1 ? "lead_bp_jit_cluster" : "lead_bp_jit";
+  if (cudaLibraryGetKernel(&kern, lib, name) != cudaSuccess ||
+      cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs.bp_smem[prec]) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, hs.bp_block, hs.bp_smem[prec]) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaLibraryUnload(lib);
+    return LEAD_ECUDA;
+  }
+  ds.bp_module[prec] = lib;
+  ds.bp_func[prec] = kern;
+  ds.bp_per_sm[prec] = per_sm;
+  return LEAD_OK;
+}
+
+}  // namespace
+
 int jit_compile(lead_code* code, std::string* log_out) {
   for (int side = 0; side < 2; ++side) {
-    HostSide& hs = code->side[side];
-    if (!hs.bp_cubin.empty()) continue;
-    const Geometry g = bp_geometry(code, side);
-    if (g.block > 1024 || (size_t)code->nl * g.ts >= 32768 || g.smem > 227u * 1024u) return LEAD_EINVAL;
-    const std::string src = prelude(code, side, g) + kLeadJitSource;
-    nvrtcProgram prog;
-    if (nvrtcCreateProgram(&prog, src.c_str(), "lead_bp_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
-      return LEAD_ECUDA;
-    // LEAD_JIT_PTXAS_VERBOSE=1 adds the assembler's register / spill report to the log
-    const char* verbose = std::getenv("LEAD_JIT_PTXAS_VERBOSE");
-    // registers per thread that let LEAD_MINBLOCKS CTAs of this size share an SM
-    const int maxreg = std::min(255, (65536 / (g.block * g.minblocks)) & ~7);
-    const std::string regopt = "--maxrregcount=" + std::to_string(maxreg);
-    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=false", "-lineinfo",
-                          regopt.c_str(), "--ptxas-options=-v"};
-    const int nopts = (verbose && verbose[0] == '1') ? 6 : 5;
-    const nvrtcResult rc = nvrtcCompileProgram(prog, nopts, opts);
-    size_t logn = 0;
-    nvrtcGetProgramLogSize(prog, &logn);
-    std::string log(logn, '\0');
-    if (logn) nvrtcGetProgramLog(prog, &log[0]);
-    if (log_out) {
-      std::ostringstream gs;
-      gs << "side " << side << ": " << (g.cluster > 1 ? "cluster of " : "") << g.cluster << " CTA(s) x "
-         << g.block << " threads, " << g.ts << " slots per CTA row, " << g.spb << " shot(s) per CTA, "
-         << g.smem << " B shared memory, " << g.minblocks << " CTA(s) per SM, <= " << maxreg
-         << " registers\n";
-      *log_out += gs.str() + log;
-    }
-    if (rc != NVRTC_SUCCESS) {
-      nvrtcDestroyProgram(&prog);
-      return LEAD_ECUDA;
-    }
-    size_t n = 0;
-    nvrtcGetCUBINSize(prog, &n);
-    hs.bp_cubin.resize(n);
-    nvrtcGetCUBIN(prog, hs.bp_cubin.data());
-    nvrtcDestroyProgram(&prog);
-    hs.bp_block = g.block;
-    hs.bp_smem = g.smem;
-    hs.bp_spb = g.spb;
-    hs.bp_cluster = g.cluster;
+    const int rc = compile_one(code, side, LEAD_PREC_FP32, log_out);
+    if (rc != LEAD_OK) return rc;
   }
   return LEAD_OK;
 }
 
 int jit_load(lead_code* code) {
   for (int side = 0; side < 2; ++side) {
-    HostSide& hs = code->side[side];
-    DeviceSide& ds = code->dside[side];
-    if (ds.bp_func) continue;
-    cudaLibrary_t lib = nullptr;
-    cudaKernel_t kern = nullptr;
-    if (cudaLibraryLoadData(&lib, hs.bp_cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess)
-      return LEAD_ECUDA;
-    int per_sm = 0;
-    const char* name = hs.bp_cluster > 1 ? "lead_bp_jit_cluster" : "lead_bp_jit";
-    if (cudaLibraryGetKernel(&kern, lib, name) != cudaSuccess ||
-        cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs.bp_smem) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, hs.bp_block, hs.bp_smem) !=
-            cudaSuccess ||
-        per_sm < 1) {
-      cudaLibraryUnload(lib);
-      return LEAD_ECUDA;
-    }
-    ds.bp_module = lib;
-    ds.bp_func = kern;
-    ds.bp_per_sm = per_sm;
+    const int rc = load_one(code, side, LEAD_PREC_FP32);
+    if (rc != LEAD_OK) return rc;
   }
   return LEAD_OK;
 }
 
-void jit_unload(lead_code* code) {
-  for (auto& ds : code->dside) {
-    if (ds.bp_module) cudaLibraryUnload(static_cast<cudaLibrary_t>(ds.bp_module));
-    ds.bp_module = nullptr;
-    ds.bp_func = nullptr;
-  }
+int jit_ensure(const lead_code* ccode, int side, int prec) {
+  lead_code* code = const_cast<lead_code*>(ccode);   // the kernel cache is not part of the code's value
+  if (prec < 0 || prec >= kPrecModes) return LEAD_EINVAL;
+  std::lock_guard<std::mutex> lock(code->jit_mu);
+  int rc = compile_one(code, side, prec, nullptr);
+  if (rc != LEAD_OK) return rc;
+  return load_one(code, side, prec);
 }
 
-int jit_launch_bp(const lead_code* code, int side, const BPJitArgs& args, int sm_count, void* stream) {
+void jit_unload(lead_code* code) {
+  for (auto& ds : code->dside)
+    for (int prec = 0; prec < kPrecModes; ++prec) {
+      if (ds.bp_module[prec]) cudaLibraryUnload(static_cast<cudaLibrary_t>(ds.bp_module[prec]));
+      ds.bp_module[prec] = nullptr;
+      ds.bp_func[prec] = nullptr;
+    }
+}
+
+int jit_launch_bp(const lead_code* code, int side, int prec, const BPJitArgs& args, int sm_count, void* stream) {
   const HostSide& hs = code->side[side];
   const DeviceSide& ds = code->dside[side];
-  if (!ds.bp_func) return LEAD_ESTATE;
+  if (prec < 0 || prec >= kPrecModes) return LEAD_EINVAL;
+  if (prec != LEAD_PREC_FP32) {          // loaded on first use, under the code's lock
+    const int rc = jit_ensure(code, side, prec);
+    if (rc != LEAD_OK) return rc;
+  } else if (!ds.bp_func[prec]) {
+    return LEAD_ESTATE;
+  }
   const long long groups = (args.shots + hs.bp_spb - 1) / hs.bp_spb;     // shots per CTA or per cluster
-  const long long units = std::max<long long>(1, ((long long)sm_count * ds.bp_per_sm) / hs.bp_cluster);
+  const long long units = std::max<long long>(1, ((long long)sm_count * ds.bp_per_sm[prec]) / hs.bp_cluster);
   const long long blocks = std::min<long long>(groups, units) * hs.bp_cluster;
   BPJitArgs a = args;
   void* params[] = {&a};
-  if (cudaLaunchKernel(ds.bp_func, dim3((unsigned)blocks), dim3(hs.bp_block), params, hs.bp_smem,
+  if (cudaLaunchKernel(ds.bp_func[prec], dim3((unsigned)blocks), dim3(hs.bp_block), params, hs.bp_smem[prec],
                        static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return LEAD_ECUDA;
   return LEAD_OK;
@@ -204,7 +293,12 @@ int jit_launch_bp(const lead_code* code, int side, const BPJitArgs& args, int sm
 extern "C" int lead_code_compile(lead_code* code, char* log, size_t log_bytes) {
   if (!code) return LEAD_EINVAL;
   std::string msg;
-  const int rc = lead::jit_compile(code, &msg);
+  int rc = LEAD_OK;
+  for (int prec = 0; prec < lead::kPrecModes && rc == LEAD_OK; ++prec)
+    for (int side = 0; side < 2 && rc == LEAD_OK; ++side) {
+      std::lock_guard<std::mutex> lock(code->jit_mu);
+      rc = lead::compile_one(code, side, prec, &msg);
+    }
   if (log && log_bytes) {
     const size_t n = std::min(log_bytes - 1, msg.size());
     std::memcpy(log, msg.data(), n);

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -15,6 +16,7 @@ constexpr int kMaxDelta = 6;          // local views of at most 36 qubits (64-bi
 constexpr int kMaxLocalRows = 12;     // m_l <= 12 local checks per vertex (2^m_l-entry tables)
 constexpr int kMaxSupport = 26;       // local check rows of weight <= 26 (packed sign bits)
 constexpr int kMaxIter = 64;
+constexpr int kPrecModes = 3;         // LEAD_PREC_FP32, LEAD_PREC_BF16, LEAD_PREC_FP16
 
 // Per-side structure that kernels receive by value.
 struct SideParams {
@@ -41,9 +43,9 @@ struct DeviceSide {
   uint8_t* xcls = nullptr;       // row patterns of every class f = R_B x (class-major, increasing)
   uint32_t* cbase = nullptr;     // 2^m_l: one row-image matrix F with R_A F = S per local syndrome
   uint32_t* ckern = nullptr;     // row-image matrices with R_A F = 0, increasing
-  void* bp_module = nullptr;     // cudaLibrary_t of the specialised min-sum kernel
-  void* bp_func = nullptr;       // its cudaKernel_t
-  int bp_per_sm = 0;             // resident CTAs per SM
+  void* bp_module[kPrecModes] = {};   // cudaLibrary_t of the specialised min-sum kernel, per mode
+  void* bp_func[kPrecModes] = {};     // its cudaKernel_t
+  int bp_per_sm[kPrecModes] = {};     // resident CTAs per SM
 };
 
 struct HostSide {
@@ -63,9 +65,9 @@ struct HostSide {
   std::vector<uint8_t> xcls;
   std::vector<uint32_t> cbase, ckern;
   SideParams params{};
-  std::vector<char> bp_cubin;        // specialised min-sum kernel (NVRTC output)
+  std::vector<char> bp_cubin[kPrecModes];   // specialised min-sum kernel per mode (NVRTC output)
   int bp_block = 0, bp_spb = 0, bp_cluster = 1;
-  size_t bp_smem = 0;
+  size_t bp_smem[kPrecModes] = {};
 };
 
 }  // namespace lead
@@ -80,6 +82,7 @@ struct lead_code {
   int32_t device = -1;
   lead::DeviceSide dside[2];
   float* d_llr = nullptr;            // prior-LLR interpolation table: node values, then slopes
+  std::mutex jit_mu;                 // guards the lazily compiled kernels of the 16-bit modes
 };
 
 namespace lead {
@@ -92,9 +95,11 @@ struct Geometry {               // launch geometry of the min-sum kernel for one
   int spb, cluster, ts, block, minblocks;
   size_t smem;
 };
-Geometry bp_geometry(const lead_code* code, int side);
-int jit_compile(lead_code* code, std::string* log);
+Geometry bp_geometry(const lead_code* code, int side, int prec = LEAD_PREC_FP32);
+int jit_compile(lead_code* code, std::string* log);      // binary32 kernels of both sides
+int compile_one(lead_code* code, int side, int prec, std::string* log);
 int jit_load(lead_code* code);
+int jit_ensure(const lead_code* code, int side, int prec);   // compile + load one mode on first use
 void jit_unload(lead_code* code);
-int jit_launch_bp(const lead_code* code, int side, const BPJitArgs& args, int sm_count, void* stream);
+int jit_launch_bp(const lead_code* code, int side, int prec, const BPJitArgs& args, int sm_count, void* stream);
 }  // namespace lead

@@ -337,7 +337,7 @@ int64_t pass_shots(const lead_code* code, int64_t shots) {
 
 int validate(const lead_code* code, const lead_decode_opts* o) {
   if (!o || o->side < 0 || o->side > 1 || o->max_iter < 0 || o->max_iter > kMaxIter) return LEAD_EINVAL;
-  if (!(o->alpha > 0.0f && o->alpha <= 1.0f) || o->precision != LEAD_PREC_FP32) return LEAD_EINVAL;
+  if (!(o->alpha > 0.0f && o->alpha <= 1.0f) || o->precision < 0 || o->precision >= kPrecModes) return LEAD_EINVAL;
   return LEAD_OK;
 }
 

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "liblead.so")
 
 NOISE_X, NOISE_Z, NOISE_DEPOL = 0, 1, 2
 ST_CONVERGED, ST_MAX_ITER = 1, 2
-PREC_FP32 = 0
+PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
 
 _c_int32_p = ctypes.POINTER(ctypes.c_int32)
 _c_uint8_p = ctypes.POINTER(ctypes.c_uint8)

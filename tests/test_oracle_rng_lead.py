@@ -166,3 +166,64 @@ def test_prior_f32_close_to_f64(psl7):
     _, l64 = lead.prior_f64(code, 0, syn, 0.03)
     l32 = lead.prior_f32(code, 0, syn, 0.03)
     assert np.abs(l64 - l32.astype(np.float64)).max() < 1e-4
+
+
+def _nearest_even(x, keep_bits):
+    """Brute force in binary64: the two binary32 values whose patterns end in 32-keep_bits zero
+    bits around x, and the nearer one (ties: the one whose kept pattern is even)."""
+    u = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.int64)
+    drop = 32 - keep_bits
+    lo = (u >> drop) << drop
+    hi = lo + (1 << drop)
+    flo = lo.astype(np.uint32).view(np.float32).astype(np.float64)
+    fhi = hi.astype(np.uint32).view(np.float32).astype(np.float64)
+    xv = np.asarray(x, dtype=np.float32).astype(np.float64)
+    dlo, dhi = np.abs(xv - flo), np.abs(fhi - xv)
+    pick_hi = (dhi < dlo) | ((dhi == dlo) & (((lo >> drop) & 1) == 1))
+    return np.where(pick_hi, fhi, flo).astype(np.float32)
+
+
+def test_bf16_rounding_is_nearest_even():
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.standard_normal(20000).astype(np.float32) * np.float32(30),
+                        rng.standard_normal(2000).astype(np.float32) * np.float32(1e-39),   # subnormal
+                        np.array([1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -(1.0 + 2 ** -8), 0.0, -0.0],
+                                 dtype=np.float32)])
+    got = lead.round_bf16(x)
+    want = _nearest_even(np.abs(x), 16) * np.sign(x).astype(np.float32)
+    assert (got[x != 0] == want[x != 0]).all()
+    assert list(got[-5:-2]) == [1.0, 1.0 + 2 ** -6, -1.0]               # ties to the even pattern
+    assert np.signbit(got[-1]) and not np.signbit(got[-2])
+    assert not (got.view(np.uint32) & 0xFFFF).any()                      # bfloat16 patterns
+
+
+def test_storage_rounding_modes():
+    x = np.array([0.1, -3.3, 1000.5, 1e-8], dtype=np.float32)
+    assert (lead.round_storage(x, lead.PREC_FP32) == x).all()
+    assert (lead.round_storage(x, lead.PREC_FP16) == x.astype(np.float16).astype(np.float32)).all()
+    big = np.array([7e4, -1e6, 65519.0, 65520.0], dtype=np.float32)
+    assert list(lead.round_storage(big, lead.PREC_FP16)) == [65504.0, -65504.0, 65504.0, 65504.0]
+    b = lead.round_storage(x, lead.PREC_BF16)
+    assert np.all(np.abs(b - x) <= np.abs(x) * 2.0 ** -9)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_reduced_precision_min_sum(sl3, precision):
+    """16-bit storage: zero syndrome still decodes to zero at iteration 0; every converged output
+    satisfies H e = s; every posterior returned is a value of the storage format; and the
+    failure rate stays that of binary32 storage within sampling noise (the decisions themselves
+    differ on shots where min-sum oscillates without converging)."""
+    inst, code = sl3
+    syn0 = np.zeros((2, code.HZ.shape[0]), dtype=np.uint8)
+    corr, st, it, _ = lead.decode(code, 0, syn0, 0.04, precision=precision)
+    assert not corr.any() and (st == lead.STATUS_CONVERGED).all() and (it == 0).all()
+    x, _ = philox.sample_errors(philox.NOISE_X, 0.03, 5, np.arange(400), code.n)
+    syn = philox.syndromes(code.HZ, x)
+    corr, st, it, post = lead.decode(code, 0, syn, 0.03, precision=precision)
+    conv = st == lead.STATUS_CONVERGED
+    assert (philox.syndromes(code.HZ, corr)[conv] == syn[conv]).all()
+    assert (lead.round_storage(post, precision) == post).all()
+    c32, st32, _, _ = lead.decode(code, 0, syn, 0.03)
+    f16 = (lead.check(code, 0, x, corr) != 0).mean()
+    f32 = (lead.check(code, 0, x, c32) != 0).mean()
+    assert abs(f16 - f32) < 4 * np.sqrt(f32 * (1 - f32) / len(x)) + 0.01
