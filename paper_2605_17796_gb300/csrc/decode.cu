@@ -13,6 +13,9 @@
 namespace lead {
 int check_device(const lead_code* code);
 int launch_table(const lead_code* code, int side, double p, float* table, cudaStream_t stream);
+size_t local_pair_extra_bytes(const lead_code* code, int side);
+int launch_local_pair(const lead_code* code, const lead_decode_opts* o, const uint32_t* syn, int64_t shots,
+                      void* llr, const float* table, void* extra, cudaStream_t stream);
 
 namespace {
 
@@ -203,7 +206,8 @@ extern "C" {
 size_t lead_workspace_bytes(const lead_code* code, const lead_decode_opts* opts, int64_t shots) {
   (void)shots;
   if (!code || !opts || opts->side < 0 || opts->side > 1) return 0;
-  return opts->use_lead ? lead::table_bytes(code, opts->side) : 0;
+  // the local posterior table, then (lead_local_estimate) its class bytes and pair table
+  return opts->use_lead ? lead::table_bytes(code, opts->side) + lead::local_pair_extra_bytes(code, opts->side) : 0;
 }
 
 int lead_local_estimate(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn,
@@ -216,11 +220,15 @@ int lead_local_estimate(const lead_code* code, const lead_decode_opts* opts, con
   if (shots < 0) return LEAD_EINVAL;
   if (shots == 0) return LEAD_OK;          // empty batch: nothing to read or write
   if (!syn || !llr || !workspace) return LEAD_EINVAL;
-  if (((uintptr_t)workspace & 15) || ws_bytes < table_bytes(code, opts->side)) return LEAD_EINVAL;
+  const size_t tb = table_bytes(code, opts->side);
+  if (((uintptr_t)workspace & 15) || ws_bytes < tb + local_pair_extra_bytes(code, opts->side)) return LEAD_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   float* table = static_cast<float*>(workspace);
   rc = launch_table(code, opts->side, opts->p, table, s);
   if (rc != LEAD_OK) return rc;
+  rc = launch_local_pair(code, opts, syn, shots, llr, table, static_cast<char*>(workspace) + tb, s);
+  if (rc != LEAD_EINVAL) return rc;
+  // codes the packed view coordinates cannot describe: the direct evaluation per qubit
   auto go = [&](auto prec) -> int {
     constexpr int PR = decltype(prec)::value;
     if (code->nl == 16) return launch_local<16, PR>(code, opts, syn, shots, llr, table, s);

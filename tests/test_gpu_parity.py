@@ -254,3 +254,31 @@ def test_pipeline_counts_match_oracle(codes, L):
         its += int(wit.sum())
     assert r.failures == int(fails.sum())
     assert r.iters_sum == its
+
+
+@pytest.mark.parametrize("GA,expect", [
+    # local codes whose boosted posteriors take more distinct values than the shared pair
+    # table holds (79 classes) or than a class byte holds (1 581): both take the direct merge
+    ([[1, 1, 0, 1, 1, 0], [0, 1, 1, 0, 1, 1], [1, 0, 0, 1, 0, 1]], 79),
+    ([[1, 1, 0, 1, 1, 1], [1, 1, 1, 0, 1, 0], [1, 1, 1, 1, 0, 0]], 1581)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_local_estimate_many_classes(L, GA, expect, precision):
+    import dataclasses
+    inst = dataclasses.replace(workloads.standard("PSL(2,7)", 0), GA=np.array(GA, dtype=np.uint8))
+    oc = tanner.from_instance(inst)
+    N, N1, ml = olocal.tables(oc.sides[0].RA, oc.sides[0].RB)
+    assert len(np.unique(olocal.boosted_table_f32(N, N1, ml, 0.05).view(np.uint32))) == expect
+    code = L.Code.from_instance(inst).prepare(0)
+    info = code.info
+    shots, p = 70, 0.05
+    e, syn = _syndromes(oc, 0, shots, p, seed=4)
+    o = L.opts(side=0, p=p, precision=precision)
+    ws = torch.zeros(code.workspace_bytes(o) // 4 + 64, dtype=torch.int32, device="cuda")
+    llr = torch.zeros((shots, info.n), dtype=torch.float32 if precision == 0 else torch.int16, device="cuda")
+    code.local_estimate(o, _dev(_words(syn, info.words_m[0])), shots, llr, ws)
+    torch.cuda.synchronize()
+    want = olead.round_storage(olead.prior_f32(oc, 0, syn, p), precision)
+    got = llr.cpu().numpy()
+    if precision == 1:
+        got = (got.view(np.uint16).astype(np.uint32) << 16).view(np.float32)
+    assert (got.view(np.uint32) == want.view(np.uint32)).all()
