@@ -135,6 +135,74 @@ def _serving(lead, rate: float, n: int, code_psl7):
     return out
 
 
+def wilson95(k: int, n: int):
+    """Wilson score interval (95 %) of a binomial proportion k / n."""
+    if n == 0:
+        return [0.0, 1.0]
+    z = 1.959963984540054
+    ph = k / n
+    den = 1 + z * z / n
+    c = (ph + z * z / (2 * n)) / den
+    h = z / den * (ph * (1 - ph) / n + z * z / (4 * n * n)) ** 0.5
+    return [max(0.0, c - h), min(1.0, c + h)]
+
+
+MODES = {"fp32": 0, "bf16": 1, "fp16": 2}
+
+
+def _local_estimation(lead, code, pipe, hbm_peak: float, shots: int):
+    """lead_local_estimate (Phases 1-2 alone: class/pair tables, per-(shot, qubit) lookups)
+    on the sweep's syndromes, per precision mode: shots/s and algorithmic HBM bytes per second
+    (syndromes read + LLRs written) over CUDA events around each call."""
+    import torch
+    info = code.info
+    stream = torch.cuda.current_stream()
+    out = {}
+    syn_bytes = info.words_m[0] * 4
+    for name, prec in MODES.items():
+        esize = 4 if prec == 0 else 2
+        llr = torch.empty((shots, info.n), dtype=torch.float32 if esize == 4 else torch.int16, device="cuda")
+        tot_ms, tot_shots = 0.0, 0
+        for p in P_SWEEP:
+            code.sample(lead.NOISE_X, p, shots, 3, 0, err_x=pipe.err[0], syn_z=pipe.syn[0])
+            o = lead.opts(side=0, p=p, precision=prec)
+            code.local_estimate(o, pipe.syn[0], shots, llr, pipe.workspace)        # warm-up
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                code.local_estimate(o, pipe.syn[0], shots, llr, pipe.workspace)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot_ms += e0.elapsed_time(e1)
+            tot_shots += 3 * shots
+        del llr
+        gbs = tot_shots * (syn_bytes + info.n * esize) / (tot_ms / 1e3) / 1e9
+        out[name] = {"shots_per_s": tot_shots / (tot_ms / 1e3), "algorithmic_gbs": gbs,
+                     "frac_of_hbm": gbs / hbm_peak, "bytes_per_shot": syn_bytes + info.n * esize}
+    return out
+
+
+def _precision_modes(lead, pipe, shots: int, p: float = 0.05):
+    """Decode throughput and logical error rate (Wilson 95 % interval) of each storage mode on
+    the same shots at one p."""
+    import torch
+    out = {}
+    for name, prec in MODES.items():
+        pipe.run(lead.NOISE_X, p, min(shots, pipe.chunk), seed=5, offset=0, precision=prec)   # loads the kernel
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = pipe.run(lead.NOISE_X, p, shots, seed=5, offset=0, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"shots_per_s": shots / (ms / 1e3), "ler": r.failures / shots,
+                     "ler_ci95": wilson95(r.failures, shots), "mean_iters": r.iters_sum / shots}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -149,6 +217,8 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=1e5)
     ap.add_argument("--serving-requests", type=int, default=30000)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--precision-shots", type=int, default=1_000_000)
+    ap.add_argument("--no-modes", action="store_true")
     args = ap.parse_args()
 
     if args.oracle_child:
@@ -334,6 +404,11 @@ def main():
                "sample": f"{args.oracle_shots_per_p} shots per p x 10 p values ({r['shots']} shots, "
                          f"{r['seconds']:.1f} s, numpy single-threaded)"}
 
+    local_est = precision = None
+    if not args.no_modes and world == 1:
+        local_est = _local_estimation(lead, code, pipe, peaks["hbm_gbs"], min(args.chunk, 1 << 20))
+        precision = _precision_modes(lead, pipe, args.precision_shots)
+
     serving = None
     if not args.no_serving and world == 1:
         serving = _serving(lead, args.serving_rate, args.serving_requests, code)
@@ -350,6 +425,9 @@ def main():
                        "l2": "inputs larger than L2 (2^20-shot chunks, 400 MB of errors)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "local_estimation": local_est,
+            "precision_modes": ({"p": 0.05, "shots": args.precision_shots, "modes": precision}
+                                if precision else None),
             "serving": serving,
             "clocks": clocks, "ler": ler,
             "mean_iters": {f"{p:.2f}": r.iters_sum / r.shots for p, r in zip(P_SWEEP, sweep)}}

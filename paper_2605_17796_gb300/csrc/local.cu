@@ -132,6 +132,13 @@ struct PairArgs {
   void* llr;                    // float, or the 16-bit pattern of the storage format
 };
 
+// Staged local syndromes are vertex-major: sv_s[v * kSvStride + shot]; the padded row of 36
+// 16-bit entries (72 bytes) spreads consecutive vertices over the banks, and four shots of one
+// vertex come with one 8-byte load.
+constexpr int kSvStride = 36;
+static_assert(kPairShotBatch % 4 == 0 && kPairShotBatch <= kSvStride && (kSvStride * 2) % 8 == 0,
+              "four-shot loads stay inside an 8-byte-aligned row");
+
 // The shots of one staged batch: every thread takes qubits tid, tid + blockDim, ... and for
 // each produces its LLR in every shot of the batch (consecutive threads on consecutive qubits,
 // so each store is coalesced; the shots give independent lookups to overlap). FAST: class and
@@ -141,29 +148,38 @@ __device__ __forceinline__ void batch_llrs(const PairArgs& a, const uint16_t* sv
                                            const OutT* pair_s, int K, int64_t b0, int nsh, OutT* out) {
   for (int i = threadIdx.x; i < a.n; i += kPairThreads) {
     const uint32_t s0 = __ldg(a.qslots + 2 * i), s1 = __ldg(a.qslots + 2 * i + 1);
-    const uint16_t* p0 = sv_s + s0 / NL;
-    const uint16_t* p1 = sv_s + s1 / NL;
+    const uint16_t* p0 = sv_s + (s0 / NL) * kSvStride;
+    const uint16_t* p1 = sv_s + (s1 / NL) * kSvStride;
     const int j0 = (int)(s0 % NL), j1 = (int)(s1 % NL);
     OutT* o = out + b0 * (int64_t)a.n + i;
-#pragma unroll 4
-    for (int sl = 0; sl < nsh; ++sl) {
-      const int e0 = p0[sl * a.order] * NL + j0;
-      const int e1 = p1[sl * a.order] * NL + j1;
-      OutT v;
-      if constexpr (FAST) {
-        v = pair_s[cls_s[e0] * K + cls_s[e1]];
-      } else {
-        const float x = merged_llr(__ldg(a.table + e0), __ldg(a.table + e1), a.alpha, a.llr_t0, a.llr_t1);
-        if constexpr (PREC == LEAD_PREC_FP32) v = x;
-        else v = (unsigned short)llr_bits<PREC>(x);
+    for (int sl = 0; sl < nsh; sl += 4) {
+      const uint2 w0 = *reinterpret_cast<const uint2*>(p0 + sl);
+      const uint2 w1 = *reinterpret_cast<const uint2*>(p1 + sl);
+      const uint32_t a0[4] = {w0.x & 0xFFFFu, w0.x >> 16, w0.y & 0xFFFFu, w0.y >> 16};
+      const uint32_t a1[4] = {w1.x & 0xFFFFu, w1.x >> 16, w1.y & 0xFFFFu, w1.y >> 16};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (sl + u < nsh) {
+          const int e0 = (int)a0[u] * NL + j0;
+          const int e1 = (int)a1[u] * NL + j1;
+          OutT v;
+          if constexpr (FAST) {
+            v = pair_s[cls_s[e0] * K + cls_s[e1]];
+          } else {
+            const float x = merged_llr(__ldg(a.table + e0), __ldg(a.table + e1), a.alpha, a.llr_t0, a.llr_t1);
+            if constexpr (PREC == LEAD_PREC_FP32) v = x;
+            else v = (unsigned short)llr_bits<PREC>(x);
+          }
+          __stcs(o + (sl + u) * (int64_t)a.n, v);
+        }
       }
-      __stcs(o + sl * (int64_t)a.n, v);
     }
   }
 }
 
 // Per batch of 32 shots the local syndromes of all vertices are extracted once into shared
-// memory ([shot][vertex]), then batch_llrs runs over the batch.
+// memory, then batch_llrs runs over the batch. Entries of shots past the batch's end are read
+// (in bounds) and never used.
 template <int NL, int PREC>
 __global__ void __launch_bounds__(kPairThreads, 3) local_pair_kernel(PairArgs a) {
   using OutT = typename std::conditional<PREC == LEAD_PREC_FP32, float, unsigned short>::type;
@@ -191,7 +207,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) local_pair_kernel(PairArgs a)
     __syncthreads();
     for (int i = threadIdx.x; i < nsh * V; i += blockDim.x) {
       const int sl = i / V, v = i - sl * V;
-      sv_s[i] = (uint16_t)bit_field(a.syn + (b0 + sl) * wm, v * ml, ml);
+      sv_s[v * kSvStride + sl] = (uint16_t)bit_field(a.syn + (b0 + sl) * wm, v * ml, ml);
     }
     __syncthreads();
     if (fast) batch_llrs<NL, PREC, true>(a, sv_s, cls_s, pair_s, K, b0, nsh, out);
@@ -203,7 +219,8 @@ __global__ void __launch_bounds__(kPairThreads, 3) local_pair_kernel(PairArgs a)
 
 size_t local_pair_extra_bytes(const lead_code* code, int side) {
   const size_t T = (size_t)(1 << code->side[side].m_l) * code->nl;
-  return (T + 255) / 256 * 256 + 256 + (size_t)kMaxClasses * kMaxClasses * 4;
+  const size_t pair = ((size_t)kMaxClasses * kMaxClasses * 4 + 255) / 256 * 256;
+  return (T + 255) / 256 * 256 + 256 + pair;     // a multiple of 256: callers may lay sides end to end
 }
 
 // Phases 1-2 through class and pair tables; `extra` (local_pair_extra_bytes, 16-byte aligned)
@@ -243,7 +260,7 @@ int launch_local_pair(const lead_code* code, const lead_decode_opts* o, const ui
   a.llr = llr;
   const size_t esize = o->precision == LEAD_PREC_FP32 ? 4 : 2;
   const size_t smem = (size_t)((T + 15) & ~15) + (size_t)kPairSmem * kPairSmem * esize +
-                      sizeof(uint16_t) * (size_t)kPairShotBatch * code->order;
+                      sizeof(uint16_t) * (size_t)kSvStride * code->order;
   if (smem > 227u * 1024u) return LEAD_EINVAL;
   auto go = [&](auto kern) -> int {
     if (smem > 48 * 1024)

@@ -92,3 +92,17 @@ def test_min_sum_kernel_specialises_without_a_gpu(lead, name):
     log = code.compile()
     assert "error" not in log.lower()
     code.compile()        # a second call is a no-op
+
+
+def test_workspace_sizes_keep_alignment():
+    """Workspace sizes are multiples of 256 bytes, so callers can place several workspaces end
+    to end (the decode server does, one per side) and keep each 16-byte aligned."""
+    from paper_2605_17796_gb300 import lead
+    import workloads
+    for name in ("SL(2,3)", "PSL(2,7)", "PSL(2,11)"):
+        code = lead.Code.from_instance(workloads.standard(name, 0))
+        for side in (0, 1):
+            for use_lead in (True, False):
+                o = lead.opts(side=side, p=0.03, use_lead=use_lead)
+                assert code.workspace_bytes(o) % 256 == 0
+                assert code.priors_workspace_bytes(o, 1000) % 256 == 0
