@@ -282,3 +282,29 @@ def test_local_estimate_many_classes(L, GA, expect, precision):
     if precision == 1:
         got = (got.view(np.uint16).astype(np.uint32) << 16).view(np.float32)
     assert (got.view(np.uint32) == want.view(np.uint32)).all()
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_local_estimate_unaligned_output(codes, L, precision):
+    """An output buffer that starts one element past an allocation boundary gets the same
+    values as an aligned one."""
+    inst, code, oc = codes["PSL(2,7)"]
+    info = code.info
+    shots, p = 37, 0.04
+    e, syn = _syndromes(oc, 0, shots, p, seed=8)
+    o = L.opts(side=0, p=p, precision=precision)
+    ws = torch.zeros(code.workspace_bytes(o) // 4 + 64, dtype=torch.int32, device="cuda")
+    dt = torch.float32 if precision == 0 else torch.int16
+    sd = _dev(_words(syn, info.words_m[0]))
+    a = torch.zeros((shots, info.n), dtype=dt, device="cuda")
+    code.local_estimate(o, sd, shots, a, ws)
+    big = torch.zeros(shots * info.n + 1, dtype=dt, device="cuda")
+    b = big[1:].view(shots, info.n)
+    code.local_estimate(o, sd, shots, b, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    want = olead.round_storage(olead.prior_f32(oc, 0, syn, p), precision)
+    got = a.cpu().numpy()
+    if precision == 2:
+        got = got.view(np.float16).astype(np.float32)
+    assert (got.view(np.uint32) == want.view(np.uint32)).all()
