@@ -188,7 +188,9 @@ int lead_sample(const lead_code* code, int32_t noise, double p, int64_t shots, u
                 uint32_t* syn_x, void* stream);
 
 /* Bytes of device workspace lead_local_estimate / lead_decode need for these options
- * (16-byte aligned start required); 0 for the baseline (use_lead = 0). */
+ * (16-byte aligned start required); 0 for the baseline (use_lead = 0). A multiple of 256.
+ * lead_decode reads only the first 2^m_l * Delta^2 * 4 bytes (rounded up to 256): the local
+ * posterior table; lead_local_estimate also uses the rest (class bytes and pair table). */
 size_t lead_workspace_bytes(const lead_code* code, const lead_decode_opts* opts, int64_t shots);
 
 /*
@@ -205,7 +207,7 @@ int lead_local_table(const lead_code* code, int32_t side, double p, float* table
  * and (v1, j1) on the side, p_i = alpha * ((q(s_v0, j0) + q(s_v1, j1)) * 1/2) in binary32,
  * clamped to [2^-23, 1 - 2^-23], and llr[shot * n + i] = ln((1 - p_i)/p_i) in binary32 (by
  * linear interpolation in a 2817-node table over the binary32 exponent and top 7 fraction bits
- * of min(p, 1-p), error below 1e-5), then stored in the format of opts->precision:
+ * of min(p, 1-p), error below 2e-5), then stored in the format of opts->precision:
  *   LEAD_PREC_FP32 float; LEAD_PREC_BF16 / LEAD_PREC_FP16 the 16-bit pattern (uint16) of the
  *   bfloat16 / binary16 rounding (to nearest even) of that binary32 value.
  *  syn (dev, shots x words_m[side]); llr (dev, shots x n elements of that format);

@@ -148,3 +148,51 @@ def autotune(entries, reps: int = 2, **kw):
             del b
         torch.cuda.empty_cache()
     return best[0], timings
+
+
+def main(argv=None):
+    """The uneven three-code batch: SL(2,3) / PSL(2,7) / PSL(2,11) with 10^4 / 2x10^5 / 10^6 shots
+    (times --scale), depolarizing p = 0.04. Prints one JSON object: the autotuned plan and its
+    replay time, every candidate's replay time, and the same work issued eagerly on one stream,
+    code after code."""
+    import argparse
+    import json
+
+    import workloads
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--reps", type=int, default=2)
+    args = ap.parse_args(argv)
+    names = ("SL(2,3)", "PSL(2,7)", "PSL(2,11)")
+    codes = [lead.Code.from_instance(workloads.standard(n, 0)).prepare(0) for n in names]
+    entries = [Entry(codes[0], int(1e4 * args.scale), seed=1), Entry(codes[1], int(2e5 * args.scale), seed=2),
+               Entry(codes[2], int(1e6 * args.scale), seed=3)]
+    total = sum(e.shots for e in entries)
+    # eager baseline: one stream, one chunk per entry, no graph
+    eager = MultiCodeBatch(entries, plan=[(0, 1)] * len(entries))
+    eager.issue()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        eager.issue()
+    e1.record()
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1) / args.reps
+    eager_summary = eager.summary()
+    del eager
+    torch.cuda.empty_cache()
+    best, timings = autotune(entries, reps=args.reps)
+    ms = best.time_replays(args.reps)
+    print(json.dumps({"entries": [{"code": n, "shots": e.shots} for n, e in zip(names, entries)],
+                      "noise": "depolarizing p=0.04, both sides", "plan": best.plan, "replay_ms": ms,
+                      "shots_per_s": total / ms * 1e3, "eager_one_stream_ms": eager_ms,
+                      "eager_shots_per_s": total / eager_ms * 1e3,
+                      "candidates": [{"plan": p, "ms": t} for p, t in timings],
+                      "summary": best.summary(), "eager_summary": eager_summary}))
+
+
+if __name__ == "__main__":
+    main()

@@ -104,12 +104,15 @@ int bp_shots_per_block(const lead_code* code) {
   return std::max(1, 256 / code->order);
 }
 
-namespace {
-
-size_t table_bytes(const lead_code* code, int side) {
+// The workspace lead_decode reads: the local posterior table (a multiple of 256 bytes).
+size_t decode_workspace_bytes(const lead_code* code, int side) {
   const size_t b = (size_t)(1 << code->side[side].m_l) * code->nl * sizeof(float);
   return (b + 255) / 256 * 256;
 }
+
+namespace {
+
+size_t table_bytes(const lead_code* code, int side) { return decode_workspace_bytes(code, side); }
 
 int validate_opts(const lead_code* code, const lead_decode_opts* o) {
   if (!o || o->side < 0 || o->side > 1) return LEAD_EINVAL;

@@ -241,10 +241,8 @@ int lead_server_create(const lead_server_config* cfg, lead_server** out) {
     s->p_side.push_back(cfg->p_side[c]);
     for (int side = 0; side < 2; ++side) {
       s->wm[side] = std::max(s->wm[side], code->side[side].params.words_m);
-      lead_decode_opts o{};
-      o.side = side;
-      o.use_lead = 1;
-      s->ws_bytes = std::max(s->ws_bytes, lead_workspace_bytes(code, &o, 0));
+      // the server only decodes: the local table, not lead_local_estimate's class tables
+      s->ws_bytes = std::max(s->ws_bytes, lead::decode_workspace_bytes(code, side));
     }
     s->wn = std::max(s->wn, code->words_n);
   }
