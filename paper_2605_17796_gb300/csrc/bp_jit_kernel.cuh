@@ -254,13 +254,14 @@ lead_bp_jit(const lead::BPJitArgs a) {
 // The same decoder for codes whose per-shot state exceeds one CTA's shared memory: a cluster of
 // LEAD_CLUSTER CTAs handles one shot, CTA rank r owning vertices r*TS .. r*TS + TS - 1 (TS =
 // LEAD_TS). A partner slot owned by another CTA is read from that CTA's shared memory through
-// the cluster's distributed shared memory (mapa + ld.shared::cluster). The iteration's two
+// the cluster's distributed shared memory (mapa to a generic address, then a plain load). The iteration's two
 // synchronisation points are cluster barriers; the shot's verdict is one flag word in rank 0,
 // OR-ed by every thread with a violated local check and read back by all threads after the
 // barrier, so every CTA of the cluster takes the same branch at every step.
-// The partner table pa32[j][v] (per global vertex v) holds: bits 0..15 the partner slot's word
-// address inside its owner CTA, bits 16..23 the owner's rank, bit 31 set when this view belongs
-// to the smaller vertex.
+// The partner table [j][v] (per global vertex v) holds the partner slot's word address inside
+// its owner CTA, the owner's rank and whether this view belongs to the smaller vertex: u16
+// entries address | rank << 13 | first << 15 when LEAD_PA16, else u32 entries address |
+// rank << 16 | first << 31.
 // ---------------------------------------------------------------------------------------------
 namespace lead_jit {
 
@@ -270,6 +271,15 @@ __device__ __forceinline__ unsigned int cluster_rank() {
   return r;
 }
 
+// Generic address of the same shared-memory location in CTA `rank` of the cluster: ordinary
+// loads through it reach that CTA's shared memory (distributed shared memory), and the compiler
+// schedules them like any other load.
+__device__ __forceinline__ const msg_t* map_rank_generic(const msg_t* p, unsigned int rank) {
+  unsigned long long out;
+  asm("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<unsigned long long>(p)), "r"(rank));
+  return reinterpret_cast<const msg_t*>(out);
+}
+
 __device__ __forceinline__ unsigned int map_rank(const void* p, unsigned int rank) {
   const unsigned int a = (unsigned int)__cvta_generic_to_shared(p);
   unsigned int out;
@@ -277,20 +287,28 @@ __device__ __forceinline__ unsigned int map_rank(const void* p, unsigned int ran
   return out;
 }
 
-__device__ __forceinline__ float ld_cluster_f32(unsigned int addr) {
-  float v;
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
-  return v;
-}
+constexpr int kPartnerGroup = 12;      // partner reads in flight per thread
 
-__device__ __forceinline__ msg_t ld_cluster_msg(unsigned int addr) {
-#if LEAD_PREC == 0
-  return ld_cluster_f32(addr);
+// Partner of slot (j, v) from the cluster partner table: word address inside the owner CTA,
+// owner rank, and whether v is the qubit's first (smaller) vertex.
+struct Partner {
+  unsigned int addr, rank;
+  bool first;
+};
+__device__ __forceinline__ Partner cluster_partner(const void* table, int j, int v, int V) {
+  Partner p;
+#if LEAD_PA16
+  const unsigned int e = __ldg(static_cast<const unsigned short*>(table) + j * V + v);
+  p.addr = e & 0x1FFFu;
+  p.rank = (e >> 13) & 3u;
+  p.first = (e >> 15) != 0;
 #else
-  unsigned short v;
-  asm volatile("ld.shared::cluster.u16 %0, [%1];" : "=h"(v) : "r"(addr) : "memory");
-  return v;
+  const unsigned int e = __ldg(static_cast<const unsigned int*>(table) + j * V + v);
+  p.addr = e & 0xFFFFu;
+  p.rank = (e >> 16) & 0xFFu;
+  p.first = (e >> 31) != 0;
 #endif
+  return p;
 }
 
 __device__ __forceinline__ unsigned int ld_cluster_u32(unsigned int addr) {
@@ -318,15 +336,14 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
   unsigned int* syn_s = smem + kMsgBytes / 4;
   unsigned int* cb = syn_s + wm;
   unsigned int* flags = cb + a.words_n;          // two words, meaningful in rank 0 only
-  const unsigned int* __restrict__ PA = reinterpret_cast<const unsigned int*>(a.pa);
 
   const unsigned int rank = cluster_rank();
   const int tid = threadIdx.x;
   const int v = (int)rank * TS + tid;            // global vertex of this thread
   const bool lane_ok = tid < TS && v < V;
-  unsigned int ubase[C];
+  const msg_t* ubase[C];          // every rank's U array, as generic addresses
 #pragma unroll
-  for (int r = 0; r < C; ++r) ubase[r] = map_rank(Us, r);
+  for (int r = 0; r < C; ++r) ubase[r] = map_rank_generic(Us, r);
   const unsigned int flag0 = map_rank(flags, 0);
   const float lam_ch = a.use_lead ? 0.0f : lead::channel_llr(a.p, a.llr_t0, a.llr_t1);
   const long long cid = blockIdx.x / C, ncl = gridDim.x / C;
@@ -352,8 +369,8 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
         if (a.lam) {
           lj = __ldg(a.lam + g0 * a.n + __ldg(a.views + v * NL + j));
         } else if (a.use_lead) {
-          const unsigned int pa = __ldg(PA + j * V + v);
-          const unsigned int addr = pa & 0xFFFFu, pr = (pa >> 16) & 0xFFu;
+          const Partner pt = cluster_partner(a.pa, j, v, V);
+          const unsigned int addr = pt.addr, pr = pt.rank;
           const unsigned int jp = addr / TS, vp = pr * TS + (addr - jp * TS);
           const unsigned int svp = lead::bit_field(syn_s, vp * ML, ML);
           lj = lead::merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp), a.alpha, a.llr_t0,
@@ -370,19 +387,39 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
       unsigned long long hm = 0;
       unsigned int bad = 0;
       if (lane_ok) {
+        // partner sums in groups of kPartnerGroup slots: all reads of a group are issued before
+        // any of them is used, so their distributed-shared-memory latencies overlap
+        constexpr int G = kPartnerGroup;
 #pragma unroll
-        for (int j = 0; j < NL; ++j) {
-          const unsigned int pa = __ldg(PA + j * V + v);
-          const unsigned int addr = pa & 0xFFFFu, pr = (pa >> 16) & 0xFFu;
-          unsigned int ub = ubase[0];
+        for (int j0 = 0; j0 < NL; j0 += G) {
+          msg_t upr[G];
+          unsigned int first = 0;
 #pragma unroll
-          for (int r = 1; r < C; ++r) ub = (pr == (unsigned int)r) ? ubase[r] : ub;
-          const float up = dec((pr == rank) ? Us[addr] : ld_cluster_msg(ub + (unsigned int)sizeof(msg_t) * addr));
-          const float uo = dec(Us[j * TS + tid]);
-          const float lj = dec(Ls[j * TS + tid]);
-          const msg_t pe = enc((pa >> 31) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo));
-          Ps[j * TS + tid] = pe;
-          hm |= (unsigned long long)(dec(pe) < 0.0f) << j;
+          for (int g = 0; g < G; ++g) {
+            const int j = j0 + g;
+            if (j < NL) {
+              const Partner pt = cluster_partner(a.pa, j, v, V);
+              const unsigned int addr = pt.addr, pr = pt.rank;
+              const msg_t* ub = ubase[0];
+#pragma unroll
+              for (int r = 1; r < C; ++r) ub = (pr == (unsigned int)r) ? ubase[r] : ub;
+              upr[g] = ub[addr];    // ordered after the previous cluster barrier (memory clobber)
+              first |= (unsigned int)pt.first << g;
+            }
+          }
+#pragma unroll
+          for (int g = 0; g < G; ++g) {
+            const int j = j0 + g;
+            if (j < NL) {
+              const float up = dec(upr[g]);
+              const float uo = dec(Us[j * TS + tid]);
+              const float lj = dec(Ls[j * TS + tid]);
+              const msg_t pe =
+                  enc(((first >> g) & 1u) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo));
+              Ps[j * TS + tid] = pe;
+              hm |= (unsigned long long)(dec(pe) < 0.0f) << j;
+            }
+          }
         }
 #pragma unroll
         for (int r = 0; r < ML; ++r) bad |= (unsigned int)(__popcll(hm & kRowMask[r]) ^ (sv >> r)) & 1u;
@@ -394,7 +431,7 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
       if (conv || t >= a.max_iter) {
         if (lane_ok) {
           for (int j = 0; j < NL; ++j) {
-            if (__ldg(PA + j * V + v) >> 31) {
+            if (cluster_partner(a.pa, j, v, V).first) {
               const int q = __ldg(a.views + v * NL + j);
               if ((hm >> j) & 1) atomicOr(cb + (q >> 5), 1u << (q & 31));
               if (a.llr) a.llr[g0 * a.n + q] = dec(Ps[j * TS + tid]);

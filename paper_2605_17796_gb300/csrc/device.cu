@@ -167,8 +167,9 @@ int prepare_side(lead_code* code, int s) {
   LEAD_TRY(upload(&ds.ckern, hs.ckern));
   // min-sum kernel partner table. One CTA per shot group: thread t = shot sl * order + vertex v,
   // slot (j, t) lives at shared-memory word j * ts + t; entry = partner address | first << 15.
-  // Cluster launch: CTA rank r owns vertices r*ts .. r*ts + ts - 1; entry (u32, indexed [j][v]) =
-  // partner word address inside its owner | owner rank << 16 | first << 31.
+  // Cluster launch: CTA rank r owns vertices r*ts .. r*ts + ts - 1; entry (indexed [j][v]) =
+  // partner word address inside its owner | owner rank << 13 | first << 15 (u16, cluster_pa16),
+  // or, for larger shapes, address | owner rank << 16 | first << 31 (u32).
   {
     const Geometry g = bp_geometry(code, s);
     if (g.cluster == 1 && (size_t)nl * g.ts < 32768) {
@@ -182,6 +183,18 @@ int prepare_side(lead_code* code, int s) {
             const int t = sl * code->order + v;
             pa[(size_t)j * g.ts + t] = (uint16_t)((jp * g.ts + sl * code->order + vp) | ((raw >> 31) << 15));
           }
+      LEAD_TRY(upload(&ds.bp_pa, pa));
+    } else if (cluster_pa16(g, nl)) {
+      // cluster launch, u16 entries: partner word address | owner rank << 13 | first << 15
+      std::vector<uint16_t> pa((size_t)nl * code->order, 0);
+      for (int v = 0; v < code->order; ++v)
+        for (int j = 0; j < nl; ++j) {
+          const uint32_t raw = hs.partner[(size_t)v * nl + j];
+          const uint32_t ps = raw & 0x7FFFFFFFu;
+          const uint32_t vp = ps / nl, jp = ps % nl;
+          const uint32_t owner = vp / g.ts, tp = vp - owner * g.ts;
+          pa[(size_t)j * code->order + v] = (uint16_t)((jp * g.ts + tp) | (owner << 13) | ((raw >> 31) << 15));
+        }
       LEAD_TRY(upload(&ds.bp_pa, pa));
     } else if (g.cluster > 1) {
       std::vector<uint32_t> pa((size_t)nl * code->order, 0);

@@ -75,7 +75,8 @@ std::string prelude(const lead_code* code, int side, const Geometry& g, int prec
     << "#define LEAD_KMAX " << kmax << "\n"
     << "#define LEAD_SPB " << g.spb << "\n"
     << "#define LEAD_CLUSTER " << g.cluster << "\n"
-    << "#define LEAD_PREC " << prec << "\n";
+    << "#define LEAD_PREC " << prec << "\n"
+    << "#define LEAD_PA16 " << (cluster_pa16(g, code->nl) ? 1 : 0) << "\n";
   // the local rows touching every slot j (increasing) and j's position in each row's support
   std::vector<std::vector<std::pair<int, int>>> rows_of(code->nl);
   for (int r = 0; r < P.m_l; ++r)

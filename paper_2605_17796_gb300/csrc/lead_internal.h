@@ -97,6 +97,9 @@ struct Geometry {               // launch geometry of the min-sum kernel for one
   size_t smem;
 };
 Geometry bp_geometry(const lead_code* code, int side, int prec = LEAD_PREC_FP32);
+// Cluster launches whose slot addresses fit 13 bits and owner ranks 2 bits use a u16 partner
+// table (address | owner << 13 | first << 15): half the bytes of the u32 form, so it stays in L1.
+inline bool cluster_pa16(const Geometry& g, int nl) { return g.cluster > 1 && g.cluster <= 4 && nl * g.ts < 8192; }
 int jit_compile(lead_code* code, std::string* log);      // binary32 kernels of both sides
 int compile_one(lead_code* code, int side, int prec, std::string* log);
 int jit_load(lead_code* code);
