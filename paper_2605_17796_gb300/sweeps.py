@@ -1,0 +1,69 @@
+"""Logical-error-rate sweeps over the scaling parameter alpha (Phase 2, Sec. III-B and IV-C).
+
+    python -m paper_2605_17796_gb300.sweeps --code "PSL(2,7)" --p 0.005,0.01,0.02,0.03 \
+        --alpha 1,0.5,0.1,0.01 --shots 200000 [--noise x|depol] [--precision 0]
+
+For every (alpha, p) it decodes the same seeded shots with LEAD and prints one JSON line: the
+logical error rate with its Wilson 95 % interval, the fraction of shots whose min-sum did not
+converge, and the mean global iterations. One line per p is added for the standalone min-sum
+baseline (alpha = null) on the same shots. Sec. IV-C's experiment is alpha = 1 against
+alpha = 0.01 across the noise range.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+from . import lead
+from .pipeline import Pipeline
+
+
+def wilson95(k: int, n: int):
+    """Wilson score interval (95 %) of a binomial proportion k / n."""
+    z = 1.959963984540054
+    ph = k / n
+    den = 1 + z * z / n
+    c = (ph + z * z / (2 * n)) / den
+    h = z / den * (ph * (1 - ph) / n + z * z / (4 * n * n)) ** 0.5
+    return [max(0.0, c - h), min(1.0, c + h)]
+
+
+def sweep(code: lead.Code, ps, alphas, shots: int, noise: int = lead.NOISE_X, precision: int = lead.PREC_FP32,
+          chunk: int = 1 << 18, seed: int = 0, baseline: bool = True):
+    """Yields one result dict per (alpha, p) and, with baseline, per p for plain min-sum."""
+    pipe = Pipeline(code, min(chunk, shots), code.info.prepared_device)
+    configs = [(a, True) for a in alphas] + ([(None, False)] if baseline else [])
+    for p in ps:
+        for alpha, use_lead in configs:
+            r = pipe.run(noise, p, shots, seed=seed, offset=0, alpha=alpha if alpha else 1.0, use_lead=use_lead,
+                         precision=precision)
+            yield {"p": p, "alpha": alpha, "decoder": "LEAD" if use_lead else "min-sum", "shots": shots,
+                   "ler": r.failures / shots, "ler_ci95": wilson95(r.failures, shots),
+                   "not_converged": r.not_converged / shots, "mean_iters": r.iters_sum / shots,
+                   "precision": precision}
+
+
+def main(argv=None):
+    import workloads
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--code", default="PSL(2,7)")
+    ap.add_argument("--p", default="0.005,0.01,0.015,0.02,0.03")
+    ap.add_argument("--alpha", default="1,0.5,0.1,0.01")
+    ap.add_argument("--shots", type=int, default=200_000)
+    ap.add_argument("--noise", choices=["x", "depol"], default="x")
+    ap.add_argument("--precision", type=int, default=lead.PREC_FP32)
+    ap.add_argument("--no-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    code = lead.Code.from_instance(workloads.standard(args.code, 0)).prepare(0)
+    noise = lead.NOISE_X if args.noise == "x" else lead.NOISE_DEPOL
+    ps = [float(x) for x in args.p.split(",")]
+    alphas = [float(x) for x in args.alpha.split(",")]
+    for row in sweep(code, ps, alphas, args.shots, noise, args.precision, baseline=not args.no_baseline):
+        row["code"] = args.code
+        row["noise"] = args.noise
+        print(json.dumps(row), flush=True)
+
+
+if __name__ == "__main__":
+    main()
