@@ -65,6 +65,10 @@ extern "C" {
 #define LEAD_PREC_FP16    2  /* LLRs stored as IEEE binary16 (round to nearest even, saturating
                                 at +-65504), FP32 arithmetic                                    */
 
+/* local decoders of Phase 1 (lead_decode_opts.estimator) */
+#define LEAD_EST_EXACT    0  /* exact posterior of the local coset, ML hard decision (default)   */
+#define LEAD_EST_MINSUM   1  /* local min-sum BP, at most Delta^2 iterations (the paper's BP part) */
+
 typedef struct lead_code lead_code;   /* opaque; immutable after lead_build_code */
 
 /* A finite group given by its Cayley table: mul[i * order + j] = index of g_i g_j (host). */
@@ -96,6 +100,7 @@ typedef struct {
   int32_t precision;      /* LEAD_PREC_*: storage format of the LLRs (see each entry point)       */
   float   alpha;          /* Phase-2 scaling, 0 < alpha <= 1 (Sec. III-B; 1 is the default)      */
   double  p;              /* channel marginal of this side's error type, 0 < p < 1/2              */
+  int32_t estimator;      /* LEAD_EST_*: the local decoder of Phase 1 (0 = exact)                 */
 } lead_decode_opts;
 
 /*
@@ -201,6 +206,25 @@ size_t lead_workspace_bytes(const lead_code* code, const lead_decode_opts* opts,
  * coset member (the confidence boost of Algorithm 1). 0 < p < 1/2.
  */
 int lead_local_table(const lead_code* code, int32_t side, double p, float* table, void* stream);
+
+/*
+ * lead_local_table_est -- the Phase-1 table of either local decoder (Alg. 1, LocalDecoder).
+ * With a uniform channel prior a local decoder's output depends only on the local syndrome, so
+ * every Phase-1 result of a side is one row of this 2^m_l x Delta^2 table.
+ *  LEAD_EST_EXACT: as lead_local_table.
+ *  LEAD_EST_MINSUM: flooding min-sum BP on the vertex's local checks (the global decoder's
+ *    rules and binary32 order of operations, channel LLR lambda_f32(p) on every position), at
+ *    most Delta^2 iterations (the paper runs its BP decoders up to the code length). Soft output
+ *    q_j = 1/(1 + e^post_j): the binary32 posterior clamped to [-88, 88], e^x in binary64 by
+ *    Cody-Waite reduction and a Taylor series with round-to-nearest operations, add and divide
+ *    in binary64, one rounding to binary32. The boost max(q_j, 1/2) on the bits of the hard
+ *    decision applies only when that decision satisfies the local syndrome (Alg. 1 Phase 1).
+ *  iters (dev, 2^m_l int32, nullable): local iterations used per syndrome, | 1 << 16 when the
+ *    local decision satisfied its syndrome (the exact estimator reports 1 | 1 << 16).
+ * Errors: LEAD_EINVAL, LEAD_ESTATE, LEAD_ECUDA.
+ */
+int lead_local_table_est(const lead_code* code, int32_t side, double p, int32_t estimator, float* table,
+                         int32_t* iters, void* stream);
 
 /*
  * lead_local_estimate -- Phases 1 and 2 (Algorithm 1): for every qubit i with views (v0, j0)

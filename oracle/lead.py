@@ -54,6 +54,7 @@ from .tanner import TannerCode
 STATUS_CONVERGED = 1
 STATUS_MAX_ITER = 2
 PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
+EST_EXACT, EST_MINSUM = 0, 1      # local decoders of Phase 1
 
 
 def round_bf16(x: np.ndarray) -> np.ndarray:
@@ -107,11 +108,16 @@ def prior_f64(code: TannerCode, side_id: int, syn: np.ndarray, p: float, alpha: 
     return ph, np.log((1.0 - pc) / pc)
 
 
-def prior_f32(code: TannerCode, side_id: int, syn: np.ndarray, p: float, alpha: float = 1.0):
-    """Phases 1-2 on the binary32 decision track: returns llr (S, n) float32."""
+def prior_f32(code: TannerCode, side_id: int, syn: np.ndarray, p: float, alpha: float = 1.0,
+              estimator: int = EST_EXACT):
+    """Phases 1-2 on the binary32 decision track: returns llr (S, n) float32. estimator selects
+    the local decoder: the exact posterior (EST_EXACT) or local min-sum BP (EST_MINSUM)."""
     side = code.sides[side_id]
-    N, N1, ml = local.tables(side.RA, side.RB)
-    lut = local.boosted_table_f32(N, N1, ml, p)
+    if estimator == EST_MINSUM:
+        lut = local_minsum_tables(side.RA, side.RB, p)[0]
+    else:
+        N, N1, ml = local.tables(side.RA, side.RB)
+        lut = local.boosted_table_f32(N, N1, ml, p)
     sv = local_syndromes(side, syn)
     qv = side.qubit_views
     q0 = lut[sv[:, qv[:, 0, 0]], qv[:, 0, 1]]
@@ -271,10 +277,11 @@ def min_sum(H: np.ndarray, block: int, syn: np.ndarray, llr: np.ndarray, max_ite
 
 
 def decode(code: TannerCode, side_id: int, syn: np.ndarray, p: float, alpha: float = 1.0,
-           max_iter: int = 32, use_lead: bool = True, precision: int = PREC_FP32):
+           max_iter: int = 32, use_lead: bool = True, precision: int = PREC_FP32,
+           estimator: int = EST_EXACT):
     """Algorithm 1 on one side (use_lead=False: the standalone min-sum baseline)."""
     if use_lead:
-        lam = prior_f32(code, side_id, syn, p, alpha)
+        lam = prior_f32(code, side_id, syn, p, alpha, estimator)
     else:
         lam = channel_prior_f32(code.n, syn.shape[0], p)
     side = code.sides[side_id]
@@ -297,3 +304,39 @@ def check(code: TannerCode, side_id: int, err: np.ndarray, corr: np.ndarray) -> 
             x[hit] ^= R[i]
     logical = x.any(axis=1) & ~bad_syn
     return (bad_syn.astype(np.uint8) | (logical.astype(np.uint8) << 1)).astype(np.uint8)
+
+
+def local_minsum_tables(RA: np.ndarray, RB: np.ndarray, p: float, max_iter: int | None = None):
+    """Phase 1 with local min-sum BP as the LocalDecoder (the paper's local decoders are BP based,
+    with at most as many iterations as the local code length, Sec. IV-A): for every local
+    syndrome s, flooding min-sum on the local check matrix kron(R_B, R_A) with the binary32
+    channel LLR lambda_f32(p) on every position, exactly the global rules of ``min_sum`` (one
+    vertex block), at most Delta^2 iterations. The soft output is q_j = sigmoid_f32(post_j); when
+    the hard decision satisfies the local syndrome, q_j <- max(q_j, 1/2) on its flipped bits
+    (Alg. 1 Phase 1). A uniform prior makes the result a function of s alone, so it is a table.
+    Returns (table (2^m_l, n_l) float32, iterations (2^m_l,) int32, converged (2^m_l,) bool,
+    hard decisions (2^m_l, n_l) uint8)."""
+    RA = np.asarray(RA, dtype=np.uint8)
+    RB = np.asarray(RB, dtype=np.uint8)
+    H = np.kron(RB, RA).astype(np.uint8)                 # local row r = rB * kA + rA
+    m_l, n_l = H.shape
+    S = 1 << m_l
+    syn = ((np.arange(S)[:, None] >> np.arange(m_l)[None, :]) & 1).astype(np.uint8)
+    lam = np.broadcast_to(local.llr_f32(np.array([p], dtype=np.float32)), (S, n_l)).copy()
+    corr, status, iters, post = min_sum(H, m_l, syn, lam, n_l if max_iter is None else max_iter)
+    q = local.sigmoid_f32(post)
+    conv = status == STATUS_CONVERGED
+    boost = conv[:, None] & (corr == 1)
+    q = np.where(boost, np.maximum(q, np.float32(0.5)), q).astype(np.float32)
+    return q, iters.astype(np.int32), conv, corr
+
+
+def expected_local_iterations(RA: np.ndarray, RB: np.ndarray, p: float, iters: np.ndarray) -> float:
+    """E[I_l] per vertex under i.i.d. flips with probability p: sum_s P(s) I_l(s), with P(s) from
+    the coset weight enumerators, P(s) = sum_w N_s[w] p^w (1 - p)^(n_l - w)."""
+    N, _, _ = local.tables(RA, RB)
+    n_l = N.shape[1] - 1
+    w = np.arange(n_l + 1)
+    ps = (N.astype(np.float64) * (p ** w) * ((1.0 - p) ** (n_l - w))).sum(axis=1)
+    return float((ps * np.asarray(iters, dtype=np.float64)).sum())
+

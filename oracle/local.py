@@ -36,7 +36,7 @@ coset, and brute force over the coset for sampled syndromes at Delta = 6.
 from __future__ import annotations
 
 import functools
-from math import comb
+from math import comb, factorial
 
 import numpy as np
 
@@ -322,6 +322,36 @@ def log_series_f64(x: np.ndarray) -> np.ndarray:
         s = s * w
         s = s + 2.0 / k
     return e.astype(np.float64) * LN2_D + z * s
+
+
+# Cody-Waite split of ln 2 (the fdlibm pair): LN2_HI has its low 21 bits zero (32 significant
+# bits), so k * LN2_HI is exact for |k| < 2^21, and LN2_HI + LN2_LO is ln 2 to double precision
+# and beyond.
+LN2_HI = np.array([0x3FE62E42FEE00000], dtype=np.uint64).view(np.float64)[0]
+LN2_LO = np.array([0x3DEA39EF35793C76], dtype=np.uint64).view(np.float64)[0]
+INV_LN2 = np.array([0x3FF71547652B82FE], dtype=np.uint64).view(np.float64)[0]   # nearest double to 1/ln 2
+
+
+def exp_series_f64(x: np.ndarray) -> np.ndarray:
+    """e^x for binary64 x in [-88, 88]: k = rint(x / ln 2), r = (x - k LN2_HI) - k LN2_LO
+    (|r| <= ln 2 / 2 + tiny), e^r by its Taylor series through r^14 in Horner form (truncation
+    below 1e-18), times 2^k (exact). Every step is a separate round-to-nearest binary64 operation."""
+    x = np.asarray(x, dtype=np.float64)
+    k = np.rint(x * INV_LN2)
+    r = (x - k * LN2_HI) - k * LN2_LO
+    s = np.full(x.shape, 1.0 / 87178291200.0)             # 1/14!
+    for n in range(13, -1, -1):
+        s = s * r
+        s = s + 1.0 / float(factorial(n))
+    return np.ldexp(s, k.astype(np.int64))
+
+
+def sigmoid_f32(post: np.ndarray) -> np.ndarray:
+    """q = 1 / (1 + e^post) as binary32: post (binary32) clamped to [-88, 88], then the binary64
+    exponential above, add and divide, rounded once to binary32. (The probability that a qubit is
+    flipped given its posterior LLR post = ln(P(0)/P(1)).)"""
+    x = np.clip(np.asarray(post, dtype=np.float32), np.float32(-88.0), np.float32(88.0)).astype(np.float64)
+    return (1.0 / (1.0 + exp_series_f64(x))).astype(np.float32)
 
 
 def llr_tables():

@@ -12,7 +12,8 @@
 
 namespace lead {
 int check_device(const lead_code* code);
-int launch_table(const lead_code* code, int side, double p, float* table, cudaStream_t stream);
+int launch_table(const lead_code* code, int side, double p, float* table, cudaStream_t stream, int estimator,
+                 int32_t* iters);
 size_t local_pair_extra_bytes(const lead_code* code, int side);
 int launch_local_pair(const lead_code* code, const lead_decode_opts* o, const uint32_t* syn, int64_t shots,
                       void* llr, const float* table, void* extra, cudaStream_t stream);
@@ -121,6 +122,7 @@ int validate_opts(const lead_code* code, const lead_decode_opts* o) {
   if (!(o->p > 0.0 && o->p < 0.5)) return LEAD_EINVAL;
   if (o->precision != LEAD_PREC_FP32 && o->precision != LEAD_PREC_BF16 && o->precision != LEAD_PREC_FP16)
     return LEAD_EINVAL;
+  if (o->estimator != LEAD_EST_EXACT && o->estimator != LEAD_EST_MINSUM) return LEAD_EINVAL;
   if (code->nl != 16 && code->nl != 36) return LEAD_EINVAL;
   return LEAD_OK;
 }
@@ -227,7 +229,7 @@ int lead_local_estimate(const lead_code* code, const lead_decode_opts* opts, con
   if (((uintptr_t)workspace & 15) || ws_bytes < tb + local_pair_extra_bytes(code, opts->side)) return LEAD_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   float* table = static_cast<float*>(workspace);
-  rc = launch_table(code, opts->side, opts->p, table, s);
+  rc = launch_table(code, opts->side, opts->p, table, s, opts->estimator, nullptr);
   if (rc != LEAD_OK) return rc;
   rc = launch_local_pair(code, opts, syn, shots, llr, table, static_cast<char*>(workspace) + tb, s);
   if (rc != LEAD_EINVAL) return rc;
@@ -259,7 +261,7 @@ int lead_decode(const lead_code* code, const lead_decode_opts* opts, const uint3
     if (!workspace || ((uintptr_t)workspace & 15) || ws_bytes < table_bytes(code, opts->side))
       return LEAD_EINVAL;
     table = static_cast<float*>(workspace);
-    rc = launch_table(code, opts->side, opts->p, table, s);
+    rc = launch_table(code, opts->side, opts->p, table, s, opts->estimator, nullptr);
     if (rc != LEAD_OK) return rc;
   }
   return launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s, nullptr);
@@ -324,7 +326,7 @@ extern "C" int lead_decode_noalloc(const lead_code* code, const lead_decode_opts
   if (!syn || !corr || !status) return LEAD_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   if (opts->use_lead) {
-    rc = launch_table(code, opts->side, opts->p, table, s);
+    rc = launch_table(code, opts->side, opts->p, table, s, opts->estimator, nullptr);
     if (rc != LEAD_OK) return rc;
   }
   return launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s, nullptr);

@@ -123,6 +123,108 @@ __global__ void table_kernel(int nl, int m_l, double r, const int32_t* __restric
   }
 }
 
+// e^x for binary64 x in [-88, 88]: Cody-Waite reduction k = rint(x / ln 2), r = (x - k LN2_HI) -
+// k LN2_LO with the fdlibm split of ln 2 (LN2_HI has 21 trailing zero bits, so k LN2_HI is exact),
+// e^r by its Taylor series through r^14 in Horner form, times 2^k (exact). Separate
+// round-to-nearest binary64 operations throughout.
+__device__ __forceinline__ double exp_series_f64(double x) {
+  const double kInvLn2 = __longlong_as_double(0x3FF71547652B82FEll);
+  const double kLn2Hi = __longlong_as_double(0x3FE62E42FEE00000ll);
+  const double kLn2Lo = __longlong_as_double(0x3DEA39EF35793C76ll);
+  constexpr double kInvFact[15] = {1.0 / 1.0, 1.0 / 1.0, 1.0 / 2.0, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0,
+                                   1.0 / 720.0, 1.0 / 5040.0, 1.0 / 40320.0, 1.0 / 362880.0,
+                                   1.0 / 3628800.0, 1.0 / 39916800.0, 1.0 / 479001600.0,
+                                   1.0 / 6227020800.0, 1.0 / 87178291200.0};
+  const double k = rint(__dmul_rn(x, kInvLn2));
+  const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(k, kLn2Hi)), __dmul_rn(k, kLn2Lo));
+  double s = kInvFact[14];
+  for (int n = 13; n >= 0; --n) s = __dadd_rn(__dmul_rn(s, r), kInvFact[n]);
+  return ldexp(s, (int)k);
+}
+
+// q = 1 / (1 + e^post) in binary32 from a binary32 posterior LLR (clamped to [-88, 88]).
+__device__ __forceinline__ float sigmoid_f32(float post) {
+  const double x = (double)fminf(fmaxf(post, -88.0f), 88.0f);
+  return __double2float_rn(__ddiv_rn(1.0, __dadd_rn(1.0, exp_series_f64(x))));
+}
+
+__global__ void fill_i32_kernel(int32_t* __restrict__ out, int n, int32_t value) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = value;
+}
+
+// Phase 1 with local min-sum BP as the LocalDecoder, one thread per local syndrome s: flooding
+// min-sum on the vertex's local checks with the binary32 channel LLR on every position and the
+// global decoder's rules (c2v = signed minimum over the other positions, sign bits and the
+// syndrome bit; U_j = sum of the messages of the rows containing j in increasing row order,
+// from 0; post_j = lambda + U_j; e_j = [post_j < 0]; iteration 0 tests the prior; stop at the
+// first t with H_v e = s, at most max_iter iterations). q_j = sigmoid(post_j), raised to 1/2 on
+// the bits of e when H_v e = s. iters[s] (nullable) = t | converged << 16.
+__global__ void minsum_table_kernel(SideParams P, int nl, double p, const float* __restrict__ t0,
+                                    const float* __restrict__ t1, int max_iter, float* __restrict__ table,
+                                    int32_t* __restrict__ iters) {
+  const int S = 1 << P.m_l;
+  const float lam = channel_llr(p, t0, t1);
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+    float post[kMaxDelta * kMaxDelta];
+    float c2v[kMaxLocalRows][kMaxSupport];
+    for (int j = 0; j < nl; ++j) post[j] = lam;
+    for (int r = 0; r < P.m_l; ++r)
+      for (int k = 0; k < P.supp_len[r]; ++k) c2v[r][k] = 0.0f;
+    bool conv = false;
+    int t = 0;
+    for (;; ++t) {
+      if (t > 0) {
+        for (int r = 0; r < P.m_l; ++r) {
+          const int L = P.supp_len[r];
+          float n1 = __int_as_float(0x7F800000), n2 = __int_as_float(0x7F800000);
+          int am = -1;
+          unsigned int negs = 0, par = (s >> r) & 1u;
+          for (int k = 0; k < L; ++k) {
+            const float v = __fsub_rn(post[P.supp[r][k]], c2v[r][k]);
+            const float m = fabsf(v);
+            const unsigned int neg = __float_as_uint(v) >> 31;
+            negs |= neg << k;
+            par ^= neg;
+            if (m < n1) {
+              n2 = n1;
+              n1 = m;
+              am = k;
+            } else if (m < n2) {
+              n2 = m;
+            }
+          }
+          for (int k = 0; k < L; ++k) {
+            const float mag = (k == am) ? n2 : n1;
+            c2v[r][k] = ((par ^ (negs >> k)) & 1u) ? -mag : mag;
+          }
+        }
+        float U[kMaxDelta * kMaxDelta];
+        for (int j = 0; j < nl; ++j) U[j] = 0.0f;
+        for (int r = 0; r < P.m_l; ++r)
+          for (int k = 0; k < P.supp_len[r]; ++k) U[P.supp[r][k]] = __fadd_rn(U[P.supp[r][k]], c2v[r][k]);
+        for (int j = 0; j < nl; ++j) post[j] = __fadd_rn(lam, U[j]);
+      }
+      unsigned long long e = 0;
+      for (int j = 0; j < nl; ++j) e |= (unsigned long long)(post[j] < 0.0f) << j;
+      bool ok = true;
+      for (int r = 0; r < P.m_l; ++r) ok &= ((unsigned int)(__popcll(e & P.rowmask[r]) & 1) == ((s >> r) & 1u));
+      if (ok) {
+        conv = true;
+        break;
+      }
+      if (t >= max_iter) break;
+    }
+    unsigned long long e = 0;
+    for (int j = 0; j < nl; ++j) e |= (unsigned long long)(post[j] < 0.0f) << j;
+    for (int j = 0; j < nl; ++j) {
+      float q = sigmoid_f32(post[j]);
+      if (conv && ((e >> j) & 1)) q = fmaxf(q, 0.5f);
+      table[(size_t)s * nl + j] = q;
+    }
+    if (iters) iters[s] = t | (conv ? 0x10000 : 0);
+  }
+}
+
 // Nodes and slopes of lambda(p) = ln((1 - p)/p) on [2^-23, 1/2] (see llr_interp), from the
 // binary64 logarithm series, rounded to binary32.
 __global__ void llr_table_kernel(float* __restrict__ t0, float* __restrict__ t1) {
@@ -318,10 +420,20 @@ int check_device(const lead_code* code) {
   return cur == code->device ? LEAD_OK : LEAD_ESTATE;
 }
 
-int launch_table(const lead_code* code, int side, double p, float* table, cudaStream_t stream) {
+int launch_table(const lead_code* code, int side, double p, float* table, cudaStream_t stream, int estimator,
+                 int32_t* iters) {
   if (!(p > 0.0 && p < 0.5)) return LEAD_EINVAL;
   const HostSide& hs = code->side[side];
   const DeviceSide& ds = code->dside[side];
+  if (estimator == LEAD_EST_MINSUM) {
+    // the local code length Delta^2 bounds the iterations (the paper runs BP up to the length)
+    const int S = 1 << hs.m_l;
+    minsum_table_kernel<<<(S + 127) / 128, 128, 0, stream>>>(hs.params, code->nl, p, code->d_llr,
+                                                              code->d_llr + kLlrNodes, code->nl, table, iters);
+    LEAD_CUDA_TRY(cudaGetLastError());
+    return LEAD_OK;
+  }
+  if (estimator != LEAD_EST_EXACT) return LEAD_EINVAL;
   const double r = p / (1.0 - p);
   const int total = (1 << hs.m_l) * code->nl;
   const int threads = 256;
@@ -357,7 +469,21 @@ int lead_local_table(const lead_code* code, int32_t side, double p, float* table
   if (!code || !table || side < 0 || side > 1) return LEAD_EINVAL;
   int rc = lead::check_device(code);
   if (rc != LEAD_OK) return rc;
-  return lead::launch_table(code, side, p, table, (cudaStream_t)stream);
+  return lead::launch_table(code, side, p, table, (cudaStream_t)stream, LEAD_EST_EXACT, nullptr);
+}
+
+int lead_local_table_est(const lead_code* code, int32_t side, double p, int32_t estimator, float* table,
+                         int32_t* iters, void* stream) {
+  if (!code || !table || side < 0 || side > 1) return LEAD_EINVAL;
+  if (estimator != LEAD_EST_EXACT && estimator != LEAD_EST_MINSUM) return LEAD_EINVAL;
+  int rc = lead::check_device(code);
+  if (rc != LEAD_OK) return rc;
+  if (iters && estimator == LEAD_EST_EXACT) {       // the exact estimator is one-shot: 1, converged
+    const int S = 1 << code->side[side].m_l;
+    lead::fill_i32_kernel<<<(S + 255) / 256, 256, 0, (cudaStream_t)stream>>>(iters, S, 1 | 0x10000);
+    LEAD_CUDA_TRY(cudaGetLastError());
+  }
+  return lead::launch_table(code, side, p, table, (cudaStream_t)stream, estimator, iters);
 }
 
 }  // extern "C"

@@ -20,7 +20,6 @@
 
 namespace lead {
 int check_device(const lead_code* code);
-int launch_table(const lead_code* code, int side, double p, float* table, cudaStream_t stream);
 int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* syn, int64_t shots,
               uint32_t* corr, uint8_t* status, int32_t* iters, float* llr, const float* table,
               cudaStream_t stream, const float* lam_in);
@@ -338,6 +337,7 @@ int64_t pass_shots(const lead_code* code, int64_t shots) {
 int validate(const lead_code* code, const lead_decode_opts* o) {
   if (!o || o->side < 0 || o->side > 1 || o->max_iter < 0 || o->max_iter > kMaxIter) return LEAD_EINVAL;
   if (!(o->alpha > 0.0f && o->alpha <= 1.0f) || o->precision < 0 || o->precision >= kPrecModes) return LEAD_EINVAL;
+  if (o->estimator != LEAD_EST_EXACT) return LEAD_EINVAL;     // per-qubit priors: exact posterior only
   return LEAD_OK;
 }
 

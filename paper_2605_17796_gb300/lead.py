@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "liblead.so")
 NOISE_X, NOISE_Z, NOISE_DEPOL = 0, 1, 2
 ST_CONVERGED, ST_MAX_ITER = 1, 2
 PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
+EST_EXACT, EST_MINSUM = 0, 1
 
 _c_int32_p = ctypes.POINTER(ctypes.c_int32)
 _c_uint8_p = ctypes.POINTER(ctypes.c_uint8)
@@ -37,7 +38,8 @@ class LeadCodeInfo(ctypes.Structure):
 
 class LeadDecodeOpts(ctypes.Structure):
     _fields_ = [("side", ctypes.c_int32), ("use_lead", ctypes.c_int32), ("max_iter", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("alpha", ctypes.c_float), ("p", ctypes.c_double)]
+                ("precision", ctypes.c_int32), ("alpha", ctypes.c_float), ("p", ctypes.c_double),
+                ("estimator", ctypes.c_int32)]
 
 
 class LeadServerConfig(ctypes.Structure):
@@ -70,6 +72,8 @@ EXPORTS = {
     "lead_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_int64]),
     "lead_local_table": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
                                         ctypes.c_void_p]),
+    "lead_local_table_est": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "lead_local_estimate": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_void_p,
                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                            ctypes.c_void_p]),
@@ -248,6 +252,10 @@ class Code:
     def local_table(self, side: int, p: float, table, stream=None):
         _check("lead_local_table", LIB.lead_local_table(self._h, side, p, _ptr(table), _stream(stream)))
 
+    def local_table_est(self, side: int, p: float, estimator: int, table, iters=None, stream=None):
+        _check("lead_local_table_est", LIB.lead_local_table_est(self._h, side, p, estimator, _ptr(table),
+                                                                _ptr(iters), _stream(stream)))
+
     def local_estimate(self, opts: LeadDecodeOpts, syn, shots: int, llr, workspace, stream=None):
         ws = _ptr(workspace)
         nb = workspace.numel() * workspace.element_size() if workspace is not None else 0
@@ -296,9 +304,9 @@ class Code:
 
 
 def opts(side: int = 0, p: float = 0.05, alpha: float = 1.0, max_iter: int = 32, use_lead: bool = True,
-         precision: int = PREC_FP32) -> LeadDecodeOpts:
+         precision: int = PREC_FP32, estimator: int = EST_EXACT) -> LeadDecodeOpts:
     return LeadDecodeOpts(side=side, use_lead=1 if use_lead else 0, max_iter=max_iter, precision=precision,
-                          alpha=alpha, p=p)
+                          alpha=alpha, p=p, estimator=estimator)
 
 
 class Server:

@@ -46,7 +46,7 @@ class Pipeline:
 
     def chunk_step(self, noise: int, p: float, shots: int, seed: int, offset: int, alpha: float = 1.0,
                    max_iter: int = 32, use_lead: bool = True, with_check: bool = True,
-                   precision: int = lead.PREC_FP32):
+                   precision: int = lead.PREC_FP32, estimator: int = lead.EST_EXACT):
         """One chunk (shots <= chunk): sample, decode the sides the noise touches, check."""
         c = self.code
         sides = self.sides_for(noise)
@@ -55,7 +55,8 @@ class Pipeline:
                  syn_z=self.syn[0] if 0 in sides else None, syn_x=self.syn[1] if 1 in sides else None)
         p_side = p if noise != lead.NOISE_DEPOL else 2.0 * p / 3.0
         for s in sides:
-            o = lead.opts(side=s, p=p_side, alpha=alpha, max_iter=max_iter, use_lead=use_lead, precision=precision)
+            o = lead.opts(side=s, p=p_side, alpha=alpha, max_iter=max_iter, use_lead=use_lead, precision=precision,
+                          estimator=estimator)
             c.decode(o, self.syn[s], shots, self.corr[s], self.status[s], self.iters[s],
                      workspace=self.workspace)
             if with_check:
@@ -63,14 +64,15 @@ class Pipeline:
         return sides
 
     def run(self, noise: int, p: float, shots: int, seed: int = 0, offset: int = 0, alpha: float = 1.0,
-            max_iter: int = 32, use_lead: bool = True, precision: int = lead.PREC_FP32) -> RunResult:
+            max_iter: int = 32, use_lead: bool = True, precision: int = lead.PREC_FP32,
+            estimator: int = lead.EST_EXACT) -> RunResult:
         """Decode `shots` shots in chunks and return failure / iteration counts."""
         acc = None
         done = 0
         while done < shots:
             n = min(self.chunk, shots - done)
             sides = self.chunk_step(noise, p, n, seed, offset + done, alpha, max_iter, use_lead,
-                                    precision=precision)
+                                    precision=precision, estimator=estimator)
             fail_any = torch.zeros(n, dtype=torch.bool, device=self.device)
             logical = torch.zeros(n, dtype=torch.bool, device=self.device)
             nc = torch.zeros(n, dtype=torch.bool, device=self.device)

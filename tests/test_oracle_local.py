@@ -231,3 +231,42 @@ def test_nonuniform_ml_is_least_cost_brute_force(sl3):
         key = sum(((sel >> (b * 4 + a)) & 1) << (a * 4 + b) for a in range(4) for b in range(4))
         want = int(sel[np.lexsort((key, cost))[0]])
         assert local.ml_nonuniform(side.RA, side.RB, s, W) == want
+
+
+def test_exp_series_f64_accuracy():
+    x = np.concatenate([np.linspace(-88.0, 88.0, 400001), [0.0, 1.0, -1.0, np.log(2.0)]])
+    got = local.exp_series_f64(x)
+    ref = np.exp(x)
+    assert np.abs(got - ref).max() <= 4.5e-16 * np.abs(ref).max() or np.all(np.abs(got / ref - 1) <= 4.5e-16)
+    assert local.exp_series_f64(np.array([0.0]))[0] == 1.0
+
+
+def test_sigmoid_inverts_the_prior_llr():
+    """sigmoid(lambda(p)) = p: the binary32 LLR of p maps back to p within the LLR's error."""
+    p = np.geomspace(1e-4, 0.49, 2001).astype(np.float32)
+    q = local.sigmoid_f32(local.llr_f32(p)).astype(np.float64)
+    assert np.all(np.abs(q - p) <= 3e-5 * p)
+    assert local.sigmoid_f32(np.array([0.0], dtype=np.float32))[0] == np.float32(0.5)
+    assert local.sigmoid_f32(np.array([1e4], dtype=np.float32))[0] > 0           # clamp at 88: no underflow to 0
+
+
+@pytest.mark.parametrize("side_id", [0, 1])
+def test_local_minsum_tables(psl7, side_id):
+    """The local min-sum estimator: iteration 0 decides the zero syndrome with q = sigmoid(lambda)
+    = p; every converged decision satisfies its local syndrome and carries the boost; a table
+    with max_iter = 0 is the prior everywhere; more iterations never undo convergence."""
+    from oracle import lead
+    inst, code = psl7
+    side = code.sides[side_id]
+    p = 0.04
+    q, iters, conv, dec = lead.local_minsum_tables(side.RA, side.RB, p)
+    lam = local.llr_f32(np.array([p], dtype=np.float32))[0]
+    assert conv[0] and iters[0] == 0 and not dec[0].any()
+    assert (q[0] == local.sigmoid_f32(np.array([lam]))[0]).all()
+    H = np.kron(side.RB, side.RA).astype(np.int64)
+    s_of = ((dec.astype(np.int64) @ H.T) & 1) @ (1 << np.arange(H.shape[0]))
+    assert (s_of[conv] == np.arange(len(conv))[conv]).all()
+    assert (q[conv][dec[conv] == 1] >= 0.5).all()
+    assert iters.max() <= inst.delta ** 2
+    q0, it0, conv0, _ = lead.local_minsum_tables(side.RA, side.RB, p, max_iter=0)
+    assert (it0 == 0).all() and conv0.sum() == 1 and (q0[1:] == q[0, 0]).all()
