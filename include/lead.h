@@ -58,6 +58,7 @@ extern "C" {
 /* per-shot decode status bits */
 #define LEAD_ST_CONVERGED 1  /* the returned correction satisfies H e = s                     */
 #define LEAD_ST_MAX_ITER  2  /* no iteration up to max_iter satisfied H e = s: decoder failure */
+#define LEAD_ST_OSD       4  /* the correction was replaced by ordered-statistics decoding       */
 
 /* precision modes of lead_decode_opts.precision */
 #define LEAD_PREC_FP32    0  /* binary32 priors and messages                                   */
@@ -339,6 +340,35 @@ int lead_local_estimate_priors(const lead_code* code, const lead_decode_opts* op
 int lead_decode_priors(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn, int64_t shots,
                        const float* prior, uint32_t* corr, uint8_t* status, int32_t* iters, float* llr,
                        void* workspace, size_t ws_bytes, void* stream);
+
+/*
+ * lead_osd -- ordered-statistics post-processing (OSD-CS) of the shots whose min-sum did not
+ * converge (status without LEAD_ST_CONVERGED); the paper's global decoder is BP-OSD in the
+ * osd_cs mode of order 3 (Sec. IV-A). Per such shot, on side opts->side:
+ *  - qubits ordered by the BP posterior LLR post (ascending binary32 value through its
+ *    order-preserving integer key, -0 before +0; ties by qubit index): most likely flipped first;
+ *  - Gaussian elimination over GF(2) of H with its columns in that order and the syndrome
+ *    carried along; the pivot of a column is the first remaining row with a 1 there; pivot
+ *    columns form the basis S, the others T (same order);
+ *  - candidates: OSD-0 (e_T = 0, e_S = H_S^-1 s), each single T column, each pair among the
+ *    first `order` T columns (lexicographic); soft weight sum_{e_i = 1} W_i with
+ *    W_i = rint(2^20 lambda_i), lambda the global decoder's binary32 prior LLRs, exact integer
+ *    sums; ties to the earlier candidate;
+ *  - corr[shot] is replaced by the chosen correction (it satisfies H e = s whenever s is in the
+ *    column space of H, as for every syndrome of an error) and status[shot] gains LEAD_ST_OSD.
+ *  order 0..6; codes with n <= 4096 and m[side] <= 4096.
+ *  syn (dev, shots x words_m[side]); prior (dev, shots x n float, nullable: the channel LLR of
+ *  opts->p for every qubit; for LEAD pass lead_local_estimate's output, the prior the global
+ *  decoder used); post (dev, shots x n float): lead_decode's posterior LLRs; status (dev, in/out);
+ *  corr (dev, in/out, shots x words_n).
+ *  workspace (dev, 16-byte aligned) >= lead_osd_workspace_bytes: one m x ceil(n/64) x 8-byte
+ *  matrix per CTA slot (at most two CTAs per SM); a smaller workspace runs fewer slots.
+ * Errors: LEAD_EINVAL, LEAD_ESTATE, LEAD_ECUDA.
+ */
+size_t lead_osd_workspace_bytes(const lead_code* code, const lead_decode_opts* opts, int64_t shots);
+int lead_osd(const lead_code* code, const lead_decode_opts* opts, int32_t order, const uint32_t* syn, int64_t shots,
+             const float* prior, const float* post, uint8_t* status, uint32_t* corr, void* workspace,
+             size_t ws_bytes, void* stream);
 
 /*
  * lead_check -- success test of Sec. IV-A on one side: residual r = err + corr.

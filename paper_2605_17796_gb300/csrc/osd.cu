@@ -1,0 +1,376 @@
+// Ordered-statistics decoding (OSD-CS) after min-sum (the paper's global decoder is BP-OSD,
+// osd_cs order 3, Sec. IV-A), for the shots whose min-sum did not converge.
+//
+// One CTA per shot at a time (persistent over the shots), with the shot's row-reduced check
+// matrix in a private workspace slot (bit-packed rows, global memory):
+//   1. column order: qubits by ascending BP posterior LLR (order-preserving integer key of the
+//      binary32 value), ties by qubit index: a bitonic sort in shared memory;
+//   2. Gaussian elimination over GF(2) in that column order, the syndrome carried along; the
+//      pivot of a column is the first remaining row (current order) with a 1 there;
+//   3. candidates: OSD-0 (e_T = 0), every single non-basis column, every pair among the first
+//      `order` non-basis columns; soft weight sum_{e_i = 1} W_i with W_i = rint(2^20 lambda_i)
+//      from the global decoder's binary32 prior, exact integer sums, ties to the earlier one;
+//   4. the chosen correction replaces the shot's correction row; status gains LEAD_ST_OSD.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "lead_device.cuh"
+
+namespace lead {
+int check_device(const lead_code* code);
+
+namespace {
+
+constexpr int kOsdThreads = 512;
+constexpr int kOsdMaxN = 4096;        // sort and per-column arrays in shared memory
+constexpr int kOsdMaxM = 4096;
+constexpr int kOsdMaxOrder = 6;
+constexpr unsigned long long kNone = ~0ull;
+
+struct OsdArgs {
+  int n, m, m_l, nl, words_m, words_n, w64, order, rank_max;
+  int64_t shots;
+  const uint32_t* syn;
+  const float* prior;         // shots x n, or null: the channel LLR lam_ch for every qubit
+  float lam_ch;
+  const float* post;          // shots x n BP posterior LLRs
+  uint8_t* status;
+  uint32_t* corr;
+  const uint16_t* views;      // order x nl qubit ids
+  unsigned long long* scratch;  // gridDim.x slots of m x w64 words
+};
+
+__device__ __forceinline__ unsigned int order_key(float x) {
+  const unsigned int u = __float_as_uint(x);
+  return (u >> 31) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ int weight_of(float lam) { return __float2int_rn(__fmul_rn(lam, 1048576.0f)); }
+
+// Block-wide reductions over kOsdThreads threads (scratch: kOsdThreads / 32 entries).
+__device__ long long block_sum_ll(long long v, long long* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  long long t = 0;
+  for (int i = 0; i < kOsdThreads / 32; ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+// minimum of (cost, index) pairs packed so that the smaller cost wins, then the smaller index
+__device__ void block_min_pair(long long& cost, int& idx, long long* redc, int* redi) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long oc = __shfl_xor_sync(0xFFFFFFFFu, cost, o);
+    const int oi = __shfl_xor_sync(0xFFFFFFFFu, idx, o);
+    if (oc < cost || (oc == cost && oi < idx)) {
+      cost = oc;
+      idx = oi;
+    }
+  }
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    redc[w] = cost;
+    redi[w] = idx;
+  }
+  __syncthreads();
+  cost = redc[0];
+  idx = redi[0];
+  for (int i = 1; i < kOsdThreads / 32; ++i)
+    if (redc[i] < cost || (redc[i] == cost && redi[i] < idx)) {
+      cost = redc[i];
+      idx = redi[i];
+    }
+  __syncthreads();
+}
+
+// Shared-memory layout of one CTA (bytes from the start of dynamic shared memory).
+struct OsdLayout {
+  int np;                                  // sort size: the power of two >= n
+  size_t keys, ord, pos, wc, piv, dval, synb, ispiv, solq, misc, total;
+};
+
+__host__ __device__ inline OsdLayout osd_layout(int n, int m) {
+  OsdLayout L{};
+  L.np = 1;
+  while (L.np < n) L.np <<= 1;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = (o + bytes + 15) & ~size_t(15);
+    return at;
+  };
+  L.keys = take(sizeof(unsigned long long) * L.np);
+  L.ord = take(sizeof(uint16_t) * n);
+  L.pos = take(sizeof(uint16_t) * n);
+  L.wc = take(sizeof(int) * n);
+  L.piv = take(sizeof(uint16_t) * m);
+  L.dval = take(sizeof(int) * m);
+  L.synb = take(m);
+  L.ispiv = take(sizeof(uint32_t) * ((n + 31) / 32));
+  L.solq = take(sizeof(uint32_t) * ((n + 31) / 32));
+  L.misc = take(sizeof(long long) * 2 * (kOsdThreads / 32) + 64);
+  L.total = o;
+  return L;
+}
+
+__global__ void __launch_bounds__(kOsdThreads) osd_kernel(OsdArgs a, double p_ch, const float* __restrict__ t0,
+                                                          const float* __restrict__ t1,
+                                                          __grid_constant__ const SideParams P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const OsdLayout L = osd_layout(a.n, a.m);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(sm + L.keys);
+  uint16_t* ord = reinterpret_cast<uint16_t*>(sm + L.ord);
+  uint16_t* pos = reinterpret_cast<uint16_t*>(sm + L.pos);
+  int* Wc = reinterpret_cast<int*>(sm + L.wc);
+  uint16_t* piv = reinterpret_cast<uint16_t*>(sm + L.piv);
+  int* dval = reinterpret_cast<int*>(sm + L.dval);
+  uint8_t* synb = sm + L.synb;
+  uint32_t* ispiv = reinterpret_cast<uint32_t*>(sm + L.ispiv);
+  uint32_t* solq = reinterpret_cast<uint32_t*>(sm + L.solq);
+  long long* redc = reinterpret_cast<long long*>(sm + L.misc);
+  int* redi = reinterpret_cast<int*>(redc + kOsdThreads / 32);
+  int* sh = redi + kOsdThreads / 32;          // sh[0] pivot row, sh[1..] first non-basis columns
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = bd >> 5;
+  const int n = a.n, m = a.m, W = a.w64;
+  const int nw32 = (n + 31) / 32;
+  const float lam_ch = channel_llr(p_ch, t0, t1);
+
+  for (int64_t shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
+    if (a.status[shot] & LEAD_ST_CONVERGED) continue;      // uniform across the CTA
+    unsigned long long* mat = a.scratch + (size_t)blockIdx.x * m * W;
+    const float* post = a.post + shot * (int64_t)n;
+    const float* prior = a.prior ? a.prior + shot * (int64_t)n : nullptr;
+    // 1. column order: ascending (posterior key, qubit)
+    for (int i = tid; i < L.np; i += bd)
+      keys[i] = i < n ? ((unsigned long long)order_key(__ldg(post + i)) << 32) | (unsigned int)i : kNone;
+    for (int i = tid; i < nw32; i += bd) {
+      ispiv[i] = 0u;
+      solq[i] = 0u;
+    }
+    __syncthreads();
+    for (int k = 2; k <= L.np; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < L.np; i += bd) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const unsigned long long x = keys[i], y = keys[ixj];
+            if ((x > y) == ((i & k) == 0)) {
+              keys[i] = y;
+              keys[ixj] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    for (int c = tid; c < n; c += bd) {
+      const int q = (int)(keys[c] & 0xFFFFFFFFull);
+      ord[c] = (uint16_t)q;
+      pos[q] = (uint16_t)c;
+      Wc[c] = weight_of(prior ? __ldg(prior + q) : lam_ch);
+    }
+    for (int idx = tid; idx < m * W; idx += bd) mat[idx] = 0ull;
+    __syncthreads();
+    // 2. the check matrix with columns in that order; syndrome bits
+    for (int i = tid; i < m; i += bd) {
+      const int v = i / a.m_l, r = i - v * a.m_l;
+      unsigned long long* row = mat + (size_t)i * W;
+      for (int k = 0; k < P.supp_len[r]; ++k) {
+        const int c = pos[__ldg(a.views + v * a.nl + P.supp[r][k])];
+        row[c >> 6] |= 1ull << (c & 63);
+      }
+      synb[i] = (uint8_t)((__ldg(a.syn + shot * a.words_m + (i >> 5)) >> (i & 31)) & 1u);
+    }
+    __syncthreads();
+    // 3. elimination
+    int rank = 0;
+    for (int col = 0; col < n && rank < a.rank_max; ++col) {
+      const int wcol = col >> 6;
+      const unsigned long long bit = 1ull << (col & 63);
+      if (tid == 0) sh[0] = 0x7FFFFFFF;
+      __syncthreads();
+      for (int i = rank + tid; i < m; i += bd)
+        if (mat[(size_t)i * W + wcol] & bit) {
+          atomicMin(sh, i);
+          break;
+        }
+      __syncthreads();
+      const int pr = sh[0];
+      __syncthreads();                                     // every thread has read the pivot row
+      if (pr == 0x7FFFFFFF) continue;
+      if (pr != rank) {
+        for (int w = tid; w < W; w += bd) {
+          const unsigned long long x = mat[(size_t)pr * W + w];
+          mat[(size_t)pr * W + w] = mat[(size_t)rank * W + w];
+          mat[(size_t)rank * W + w] = x;
+        }
+        if (tid == 0) {
+          const uint8_t t = synb[pr];
+          synb[pr] = synb[rank];
+          synb[rank] = t;
+        }
+      }
+      __syncthreads();
+      const unsigned long long* prow = mat + (size_t)rank * W;
+      for (int i = warp; i < m; i += nwarps) {
+        if (i == rank) continue;
+        unsigned long long* row = mat + (size_t)i * W;
+        const unsigned long long w0 = __shfl_sync(0xFFFFFFFFu, lane == 0 ? row[wcol] : 0ull, 0);
+        if (w0 & bit) {
+          for (int w = lane; w < W; w += 32) row[w] ^= prow[w];
+          if (lane == 0) synb[i] ^= synb[rank];
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        piv[rank] = (uint16_t)col;
+        ispiv[col >> 5] |= 1u << (col & 31);
+      }
+      ++rank;
+    }
+    __syncthreads();
+    // 4. candidate costs
+    long long part = 0;
+    for (int i = tid; i < rank; i += bd) {
+      const int wp = Wc[piv[i]];
+      dval[i] = synb[i] ? -wp : wp;
+      part += synb[i] ? wp : 0;
+    }
+    const long long cost0 = block_sum_ll(part, redc);       // (contains the syncs dval needs)
+    long long bc = 0x7FFFFFFFFFFFFFFFll;
+    int bi = 0x7FFFFFFF;
+    for (int c = tid; c < n; c += bd) {
+      if ((ispiv[c >> 5] >> (c & 31)) & 1u) continue;
+      long long acc = Wc[c];
+      const int wc = c >> 6;
+      const unsigned long long bit = 1ull << (c & 63);
+      for (int i = 0; i < rank; ++i)
+        if (mat[(size_t)i * W + wc] & bit) acc += dval[i];
+      const long long cost = cost0 + acc;
+      if (cost < bc || (cost == bc && c < bi)) {
+        bc = cost;
+        bi = c;
+      }
+    }
+    block_min_pair(bc, bi, redc, redi);
+    if (tid == 0) {
+      int cnt = 0;
+      for (int c = 0; c < n && cnt < a.order; ++c)
+        if (!((ispiv[c >> 5] >> (c & 31)) & 1u)) sh[1 + cnt++] = c;
+      sh[1 + kOsdMaxOrder] = cnt;
+    }
+    __syncthreads();
+    long long wcost = cost0;
+    int kind = 0, ca = -1, cb = -1;
+    if (bi != 0x7FFFFFFF && bc < wcost) {
+      wcost = bc;
+      kind = 1;
+      ca = bi;
+    }
+    const int nt = sh[1 + kOsdMaxOrder];
+    for (int pa = 0; pa < nt; ++pa)
+      for (int pb = pa + 1; pb < nt; ++pb) {
+        const int x = sh[1 + pa], y = sh[1 + pb];
+        long long ps = 0;
+        for (int i = tid; i < rank; i += bd) {
+          const unsigned long long* row = mat + (size_t)i * W;
+          if ((((row[x >> 6] >> (x & 63)) ^ (row[y >> 6] >> (y & 63))) & 1ull) != 0) ps += dval[i];
+        }
+        const long long cost = cost0 + Wc[x] + Wc[y] + block_sum_ll(ps, redc);
+        if (cost < wcost) {
+          wcost = cost;
+          kind = 2;
+          ca = x;
+          cb = y;
+        }
+      }
+    // 5. the chosen correction, in qubit order
+    for (int i = tid; i < rank; i += bd) {
+      const unsigned long long* row = mat + (size_t)i * W;
+      unsigned int v = synb[i];
+      if (kind >= 1) v ^= (unsigned int)((row[ca >> 6] >> (ca & 63)) & 1ull);
+      if (kind == 2) v ^= (unsigned int)((row[cb >> 6] >> (cb & 63)) & 1ull);
+      if (v) {
+        const int q = ord[piv[i]];
+        atomicOr(solq + (q >> 5), 1u << (q & 31));
+      }
+    }
+    if (tid == 0) {
+      if (kind >= 1) atomicOr(solq + (ord[ca] >> 5), 1u << (ord[ca] & 31));
+      if (kind == 2) atomicOr(solq + (ord[cb] >> 5), 1u << (ord[cb] & 31));
+    }
+    __syncthreads();
+    for (int w = tid; w < a.words_n; w += bd) a.corr[shot * a.words_n + w] = w < nw32 ? solq[w] : 0u;
+    if (tid == 0) a.status[shot] = (uint8_t)(a.status[shot] | LEAD_ST_OSD);
+    __syncthreads();
+  }
+}
+
+size_t osd_slot_bytes(const lead_code* code, int side) {
+  const size_t w64 = ((size_t)code->n + 63) / 64;
+  return ((size_t)code->side[side].m * w64 * 8 + 255) / 256 * 256;
+}
+
+int osd_slots(const lead_code* code, int64_t shots) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(shots, 2 * (int64_t)sm_count(code->device)));
+}
+
+}  // namespace
+}  // namespace lead
+
+extern "C" {
+
+size_t lead_osd_workspace_bytes(const lead_code* code, const lead_decode_opts* opts, int64_t shots) {
+  if (!code || !opts || opts->side < 0 || opts->side > 1 || shots < 0 || code->device < 0) return 0;
+  return (size_t)lead::osd_slots(code, shots) * lead::osd_slot_bytes(code, opts->side);
+}
+
+int lead_osd(const lead_code* code, const lead_decode_opts* opts, int32_t order, const uint32_t* syn, int64_t shots,
+             const float* prior, const float* post, uint8_t* status, uint32_t* corr, void* workspace,
+             size_t ws_bytes, void* stream) {
+  using namespace lead;
+  int rc = check_device(code);
+  if (rc != LEAD_OK) return rc;
+  if (!opts || opts->side < 0 || opts->side > 1 || order < 0 || order > kOsdMaxOrder || shots < 0)
+    return LEAD_EINVAL;
+  const HostSide& hs = code->side[opts->side];
+  if (code->n > kOsdMaxN || hs.m > kOsdMaxM) return LEAD_EINVAL;
+  if (!prior && !(opts->p > 0.0 && opts->p < 0.5)) return LEAD_EINVAL;
+  if (shots == 0) return LEAD_OK;
+  if (!syn || !post || !status || !corr || !workspace || ((uintptr_t)workspace & 15)) return LEAD_EINVAL;
+  const size_t slot = osd_slot_bytes(code, opts->side);
+  const int slots = (int)std::min<int64_t>(osd_slots(code, shots), (int64_t)(ws_bytes / slot));
+  if (slots < 1) return LEAD_EINVAL;
+  const OsdLayout L = osd_layout(code->n, hs.m);
+  if (L.total > 227u * 1024u) return LEAD_EINVAL;
+  if (L.total > 48u * 1024u)
+    LEAD_CUDA_TRY(cudaFuncSetAttribute(osd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  OsdArgs a{};
+  a.n = code->n;
+  a.m = hs.m;
+  a.m_l = hs.m_l;
+  a.nl = code->nl;
+  a.words_m = hs.params.words_m;
+  a.words_n = code->words_n;
+  a.w64 = (code->n + 63) / 64;
+  a.order = order;
+  a.rank_max = hs.rank;
+  a.shots = shots;
+  a.syn = syn;
+  a.prior = prior;
+  a.post = post;
+  a.status = status;
+  a.corr = corr;
+  a.views = code->dside[opts->side].views;
+  a.scratch = static_cast<unsigned long long*>(workspace);
+  osd_kernel<<<slots, kOsdThreads, L.total, (cudaStream_t)stream>>>(a, opts->p > 0.0 ? opts->p : 0.25, code->d_llr,
+                                                                     code->d_llr + kLlrNodes, hs.params);
+  LEAD_CUDA_TRY(cudaGetLastError());
+  return LEAD_OK;
+}
+
+}  // extern "C"

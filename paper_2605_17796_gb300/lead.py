@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblead.so")
 
 NOISE_X, NOISE_Z, NOISE_DEPOL = 0, 1, 2
-ST_CONVERGED, ST_MAX_ITER = 1, 2
+ST_CONVERGED, ST_MAX_ITER, ST_OSD = 1, 2, 4
 PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
 EST_EXACT, EST_MINSUM = 0, 1
 
@@ -93,6 +93,10 @@ EXPORTS = {
                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                           ctypes.c_void_p]),
+    "lead_osd_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_int64]),
+    "lead_osd": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_int32, ctypes.c_void_p,
+                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "lead_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lead_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -297,6 +301,17 @@ class Code:
         _check("lead_decode_priors", LIB.lead_decode_priors(
             self._h, ctypes.byref(opts), _ptr(syn), shots, _ptr(prior), _ptr(corr), _ptr(status), _ptr(iters),
             _ptr(llr), ws, nb, _stream(stream)))
+
+    def osd_workspace_bytes(self, opts: LeadDecodeOpts, shots: int) -> int:
+        return int(LIB.lead_osd_workspace_bytes(self._h, ctypes.byref(opts), shots))
+
+    def osd(self, opts: LeadDecodeOpts, order: int, syn, shots: int, post, status, corr, prior=None,
+            workspace=None, stream=None):
+        """lead_osd: OSD-CS of the given order on the shots whose min-sum did not converge."""
+        ws = _ptr(workspace)
+        nb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        _check("lead_osd", LIB.lead_osd(self._h, ctypes.byref(opts), order, _ptr(syn), shots, _ptr(prior), _ptr(post),
+                                        _ptr(status), _ptr(corr), ws, nb, _stream(stream)))
 
     def check(self, side: int, err, corr, shots: int, fail, stream=None):
         _check("lead_check", LIB.lead_check(self._h, side, _ptr(err), _ptr(corr), shots, _ptr(fail),
