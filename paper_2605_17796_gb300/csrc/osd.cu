@@ -5,8 +5,8 @@
 // matrix in a private workspace slot (bit-packed rows, global memory):
 //   1. column order: qubits by ascending BP posterior LLR (order-preserving integer key of the
 //      binary32 value), ties by qubit index: a bitonic sort in shared memory;
-//   2. Gaussian elimination over GF(2) in that column order, the syndrome carried along; the
-//      pivot of a column is the first remaining row (current order) with a 1 there;
+//   2. Gauss-Jordan elimination over GF(2) in that column order, the syndrome carried along,
+//      blocked by 64 columns (the reduced rows are unique, so the pivot row choice is free);
 //   3. candidates: OSD-0 (e_T = 0), every single non-basis column, every pair among the first
 //      `order` non-basis columns; soft weight sum_{e_i = 1} W_i with W_i = rint(2^20 lambda_i)
 //      from the global decoder's binary32 prior, exact integer sums, ties to the earlier one;
@@ -91,7 +91,7 @@ __device__ void block_min_pair(long long& cost, int& idx, long long* redc, int* 
 // Shared-memory layout of one CTA (bytes from the start of dynamic shared memory).
 struct OsdLayout {
   int np;                                  // sort size: the power of two >= n
-  size_t keys, ord, pos, wc, piv, dval, synb, ispiv, solq, misc, total;
+  size_t keys, ord, pos, wc, piv, rowof, dval, synb, ispiv, solq, panel, amask, used, misc, total;
 };
 
 __host__ __device__ inline OsdLayout osd_layout(int n, int m) {
@@ -104,16 +104,22 @@ __host__ __device__ inline OsdLayout osd_layout(int n, int m) {
     o = (o + bytes + 15) & ~size_t(15);
     return at;
   };
-  L.keys = take(sizeof(unsigned long long) * L.np);
+  // the sort keys, later the 64 staged pivot rows of a panel (64 x ceil(n/64) words)
+  const size_t w64 = (size_t)(n + 63) / 64;
+  L.keys = take(sizeof(unsigned long long) * (L.np > (int)(64 * w64) ? L.np : 64 * w64));
   L.ord = take(sizeof(uint16_t) * n);
   L.pos = take(sizeof(uint16_t) * n);
   L.wc = take(sizeof(int) * n);
-  L.piv = take(sizeof(uint16_t) * m);
+  L.piv = take(sizeof(uint16_t) * m);          // pivot column of reduced row r
+  L.rowof = take(sizeof(uint16_t) * m);        // physical row holding reduced row r
   L.dval = take(sizeof(int) * m);
   L.synb = take(m);
   L.ispiv = take(sizeof(uint32_t) * ((n + 31) / 32));
   L.solq = take(sizeof(uint32_t) * ((n + 31) / 32));
-  L.misc = take(sizeof(long long) * 2 * (kOsdThreads / 32) + 64);
+  L.panel = take(sizeof(unsigned long long) * m);   // the current panel word of every row
+  L.amask = take(sizeof(unsigned long long) * m);   // which of the panel's pivot rows each row took
+  L.used = take(m);                                 // row already serves as a pivot
+  L.misc = take(sizeof(long long) * 2 * (kOsdThreads / 32) + 64 + 64 * sizeof(int) + 64);
   L.total = o;
   return L;
 }
@@ -128,13 +134,20 @@ __global__ void __launch_bounds__(kOsdThreads) osd_kernel(OsdArgs a, double p_ch
   uint16_t* pos = reinterpret_cast<uint16_t*>(sm + L.pos);
   int* Wc = reinterpret_cast<int*>(sm + L.wc);
   uint16_t* piv = reinterpret_cast<uint16_t*>(sm + L.piv);
+  uint16_t* rowof = reinterpret_cast<uint16_t*>(sm + L.rowof);
+  unsigned long long* panel = reinterpret_cast<unsigned long long*>(sm + L.panel);
+  unsigned long long* amask = reinterpret_cast<unsigned long long*>(sm + L.amask);
+  uint8_t* used = sm + L.used;
+  unsigned long long* qrows = keys;            // staged pivot rows (after the sort)
   int* dval = reinterpret_cast<int*>(sm + L.dval);
   uint8_t* synb = sm + L.synb;
   uint32_t* ispiv = reinterpret_cast<uint32_t*>(sm + L.ispiv);
   uint32_t* solq = reinterpret_cast<uint32_t*>(sm + L.solq);
   long long* redc = reinterpret_cast<long long*>(sm + L.misc);
   int* redi = reinterpret_cast<int*>(redc + kOsdThreads / 32);
-  int* sh = redi + kOsdThreads / 32;          // sh[0] pivot row, sh[1..] first non-basis columns
+  int* sh = redi + kOsdThreads / 32;          // sh[0..1] pivot search slots, sh[2..] first non-basis columns
+  int* kphys = sh + 16;                        // physical rows of the panel's pivots
+  uint8_t* synq = reinterpret_cast<uint8_t*>(kphys + 64);
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = bd >> 5;
   const int n = a.n, m = a.m, W = a.w64;
   const int nw32 = (n + 31) / 32;
@@ -186,59 +199,89 @@ __global__ void __launch_bounds__(kOsdThreads) osd_kernel(OsdArgs a, double p_ch
       synb[i] = (uint8_t)((__ldg(a.syn + shot * a.words_m + (i >> 5)) >> (i & 31)) & 1u);
     }
     __syncthreads();
-    // 3. elimination
+    // 3. Gauss-Jordan elimination in blocks of 64 columns (one word of every row). The reduced
+    // rows of the pivots, in pivot order, and the carried syndrome are unique for a given
+    // column order, so any pivot row may be chosen. Phase A eliminates the panel word of every
+    // row in shared memory and records, per row, which of the panel's pivot rows (as they
+    // stood at the panel's start) it took; phase B applies those sums to the full rows.
+    for (int i = tid; i < m; i += bd) used[i] = 0;
+    if (tid == 0) {
+      sh[0] = 0x7FFFFFFF;
+      sh[1] = 0x7FFFFFFF;
+    }
+    __syncthreads();
     int rank = 0;
-    for (int col = 0; col < n && rank < a.rank_max; ++col) {
-      const int wcol = col >> 6;
-      const unsigned long long bit = 1ull << (col & 63);
-      if (tid == 0) sh[0] = 0x7FFFFFFF;
-      __syncthreads();
-      for (int i = rank + tid; i < m; i += bd)
-        if (mat[(size_t)i * W + wcol] & bit) {
-          atomicMin(sh, i);
-          break;
-        }
-      __syncthreads();
-      const int pr = sh[0];
-      __syncthreads();                                     // every thread has read the pivot row
-      if (pr == 0x7FFFFFFF) continue;
-      if (pr != rank) {
-        for (int w = tid; w < W; w += bd) {
-          const unsigned long long x = mat[(size_t)pr * W + w];
-          mat[(size_t)pr * W + w] = mat[(size_t)rank * W + w];
-          mat[(size_t)rank * W + w] = x;
-        }
-        if (tid == 0) {
-          const uint8_t t = synb[pr];
-          synb[pr] = synb[rank];
-          synb[rank] = t;
-        }
+    for (int pn = 0; pn < W && rank < a.rank_max; ++pn) {
+      for (int i = tid; i < m; i += bd) {
+        panel[i] = mat[(size_t)i * W + pn];
+        amask[i] = 0ull;
       }
       __syncthreads();
-      const unsigned long long* prow = mat + (size_t)rank * W;
-      for (int i = warp; i < m; i += nwarps) {
-        if (i == rank) continue;
-        unsigned long long* row = mat + (size_t)i * W;
-        const unsigned long long w0 = __shfl_sync(0xFFFFFFFFu, lane == 0 ? row[wcol] : 0ull, 0);
-        if (w0 & bit) {
-          for (int w = lane; w < W; w += 32) row[w] ^= prow[w];
-          if (lane == 0) synb[i] ^= synb[rank];
+      int k = 0;
+      for (int b = 0; b < 64 && rank + k < a.rank_max; ++b) {
+        const int col = pn * 64 + b;
+        if (col >= n) break;
+        int* slot = sh + (b & 1);
+        for (int i = tid; i < m; i += bd)
+          if (!used[i] && ((panel[i] >> b) & 1ull)) {
+            atomicMin(slot, i);
+            break;
+          }
+        __syncthreads();
+        const int pr = *slot;
+        if (pr != 0x7FFFFFFF) {
+          const unsigned long long pp = panel[pr], ap = amask[pr] ^ (1ull << k);
+          for (int i = tid; i < m; i += bd)
+            if (i != pr && ((panel[i] >> b) & 1ull)) {
+              panel[i] ^= pp;
+              amask[i] ^= ap;
+            }
+          if (tid == 0) {
+            used[pr] = 1;
+            kphys[k] = pr;
+            piv[rank + k] = (uint16_t)col;
+            rowof[rank + k] = (uint16_t)pr;
+            ispiv[col >> 5] |= 1u << (col & 31);
+          }
+          ++k;
         }
+        __syncthreads();                                   // every thread has read this slot
+        if (tid == 0) *slot = 0x7FFFFFFF;                  // free for step b + 2
       }
-      __syncthreads();
-      if (tid == 0) {
-        piv[rank] = (uint16_t)col;
-        ispiv[col >> 5] |= 1u << (col & 31);
+      if (k > 0) {
+        for (int idx = tid; idx < k * W; idx += bd) {
+          const int kk = idx / W, w = idx - kk * W;
+          qrows[idx] = mat[(size_t)kphys[kk] * W + w];
+        }
+        for (int kk = tid; kk < k; kk += bd) synq[kk] = synb[kphys[kk]];
+        __syncthreads();
+        for (int i = warp; i < m; i += nwarps) {
+          const unsigned long long am = amask[i];
+          if (!am) continue;
+          unsigned long long* row = mat + (size_t)i * W;
+          for (int w = lane; w < W; w += 32) {
+            unsigned long long acc = 0ull;
+            for (unsigned long long r = am; r; r &= r - 1) acc ^= qrows[(__ffsll((long long)r) - 1) * W + w];
+            row[w] ^= acc;
+          }
+          if (lane == 0) {
+            unsigned int sacc = 0;
+            for (unsigned long long r = am; r; r &= r - 1) sacc ^= synq[__ffsll((long long)r) - 1];
+            synb[i] ^= (uint8_t)sacc;
+          }
+        }
+        __syncthreads();
       }
-      ++rank;
+      rank += k;
     }
     __syncthreads();
     // 4. candidate costs
     long long part = 0;
     for (int i = tid; i < rank; i += bd) {
       const int wp = Wc[piv[i]];
-      dval[i] = synb[i] ? -wp : wp;
-      part += synb[i] ? wp : 0;
+      const uint8_t si = synb[rowof[i]];
+      dval[i] = si ? -wp : wp;
+      part += si ? wp : 0;
     }
     const long long cost0 = block_sum_ll(part, redc);       // (contains the syncs dval needs)
     long long bc = 0x7FFFFFFFFFFFFFFFll;
@@ -249,7 +292,7 @@ __global__ void __launch_bounds__(kOsdThreads) osd_kernel(OsdArgs a, double p_ch
       const int wc = c >> 6;
       const unsigned long long bit = 1ull << (c & 63);
       for (int i = 0; i < rank; ++i)
-        if (mat[(size_t)i * W + wc] & bit) acc += dval[i];
+        if (mat[(size_t)rowof[i] * W + wc] & bit) acc += dval[i];
       const long long cost = cost0 + acc;
       if (cost < bc || (cost == bc && c < bi)) {
         bc = cost;
@@ -260,8 +303,8 @@ __global__ void __launch_bounds__(kOsdThreads) osd_kernel(OsdArgs a, double p_ch
     if (tid == 0) {
       int cnt = 0;
       for (int c = 0; c < n && cnt < a.order; ++c)
-        if (!((ispiv[c >> 5] >> (c & 31)) & 1u)) sh[1 + cnt++] = c;
-      sh[1 + kOsdMaxOrder] = cnt;
+        if (!((ispiv[c >> 5] >> (c & 31)) & 1u)) sh[2 + cnt++] = c;
+      sh[2 + kOsdMaxOrder] = cnt;
     }
     __syncthreads();
     long long wcost = cost0;
@@ -271,13 +314,13 @@ __global__ void __launch_bounds__(kOsdThreads) osd_kernel(OsdArgs a, double p_ch
       kind = 1;
       ca = bi;
     }
-    const int nt = sh[1 + kOsdMaxOrder];
+    const int nt = sh[2 + kOsdMaxOrder];
     for (int pa = 0; pa < nt; ++pa)
       for (int pb = pa + 1; pb < nt; ++pb) {
-        const int x = sh[1 + pa], y = sh[1 + pb];
+        const int x = sh[2 + pa], y = sh[2 + pb];
         long long ps = 0;
         for (int i = tid; i < rank; i += bd) {
-          const unsigned long long* row = mat + (size_t)i * W;
+          const unsigned long long* row = mat + (size_t)rowof[i] * W;
           if ((((row[x >> 6] >> (x & 63)) ^ (row[y >> 6] >> (y & 63))) & 1ull) != 0) ps += dval[i];
         }
         const long long cost = cost0 + Wc[x] + Wc[y] + block_sum_ll(ps, redc);
@@ -290,8 +333,8 @@ __global__ void __launch_bounds__(kOsdThreads) osd_kernel(OsdArgs a, double p_ch
       }
     // 5. the chosen correction, in qubit order
     for (int i = tid; i < rank; i += bd) {
-      const unsigned long long* row = mat + (size_t)i * W;
-      unsigned int v = synb[i];
+      const unsigned long long* row = mat + (size_t)rowof[i] * W;
+      unsigned int v = synb[rowof[i]];
       if (kind >= 1) v ^= (unsigned int)((row[ca >> 6] >> (ca & 63)) & 1ull);
       if (kind == 2) v ^= (unsigned int)((row[cb >> 6] >> (cb & 63)) & 1ull);
       if (v) {
