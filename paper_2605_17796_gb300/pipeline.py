@@ -40,14 +40,26 @@ class Pipeline:
         self.fail = [torch.zeros(chunk, dtype=torch.uint8, **kw) for _ in range(2)]
         ws = max(code.workspace_bytes(lead.opts(side=s, use_lead=True)) for s in range(2))
         self.workspace = torch.zeros(max(ws, 256) // 4 + 64, dtype=torch.int32, **kw)
+        self._osd = None          # posterior / prior / workspace buffers, made on first OSD use
+
+    def _osd_buffers(self):
+        if self._osd is None:
+            info = self.code.info
+            kw = dict(device=self.device)
+            nb = max(self.code.osd_workspace_bytes(lead.opts(side=s), self.chunk) for s in range(2))
+            self._osd = {"post": torch.zeros((self.chunk, info.n), dtype=torch.float32, **kw),
+                         "prior": torch.zeros((self.chunk, info.n), dtype=torch.float32, **kw),
+                         "ws": torch.zeros(nb // 4 + 64, dtype=torch.int32, **kw)}
+        return self._osd
 
     def sides_for(self, noise: int):
         return {lead.NOISE_X: [0], lead.NOISE_Z: [1], lead.NOISE_DEPOL: [0, 1]}[noise]
 
     def chunk_step(self, noise: int, p: float, shots: int, seed: int, offset: int, alpha: float = 1.0,
                    max_iter: int = 32, use_lead: bool = True, with_check: bool = True,
-                   precision: int = lead.PREC_FP32, estimator: int = lead.EST_EXACT):
-        """One chunk (shots <= chunk): sample, decode the sides the noise touches, check."""
+                   precision: int = lead.PREC_FP32, estimator: int = lead.EST_EXACT, osd_order=None):
+        """One chunk (shots <= chunk): sample, decode the sides the noise touches (with OSD-CS of
+        osd_order on the shots min-sum leaves unconverged, when given), check."""
         c = self.code
         sides = self.sides_for(noise)
         c.sample(noise, p, shots, seed, offset,
@@ -57,22 +69,34 @@ class Pipeline:
         for s in sides:
             o = lead.opts(side=s, p=p_side, alpha=alpha, max_iter=max_iter, use_lead=use_lead, precision=precision,
                           estimator=estimator)
-            c.decode(o, self.syn[s], shots, self.corr[s], self.status[s], self.iters[s],
-                     workspace=self.workspace)
+            if osd_order is None:
+                c.decode(o, self.syn[s], shots, self.corr[s], self.status[s], self.iters[s],
+                         workspace=self.workspace)
+            else:
+                b = self._osd_buffers()
+                post, prior = b["post"][:shots], None
+                c.decode(o, self.syn[s], shots, self.corr[s], self.status[s], self.iters[s], llr=post,
+                         workspace=self.workspace)
+                if use_lead:
+                    prior = b["prior"][:shots]
+                    po = lead.opts(side=s, p=p_side, alpha=alpha, estimator=estimator)
+                    c.local_estimate(po, self.syn[s], shots, prior, self.workspace)
+                c.osd(o, osd_order, self.syn[s], shots, post, self.status[s], self.corr[s], prior=prior,
+                      workspace=b["ws"])
             if with_check:
                 c.check(s, self.err[s], self.corr[s], shots, self.fail[s])
         return sides
 
     def run(self, noise: int, p: float, shots: int, seed: int = 0, offset: int = 0, alpha: float = 1.0,
             max_iter: int = 32, use_lead: bool = True, precision: int = lead.PREC_FP32,
-            estimator: int = lead.EST_EXACT) -> RunResult:
+            estimator: int = lead.EST_EXACT, osd_order=None) -> RunResult:
         """Decode `shots` shots in chunks and return failure / iteration counts."""
         acc = None
         done = 0
         while done < shots:
             n = min(self.chunk, shots - done)
             sides = self.chunk_step(noise, p, n, seed, offset + done, alpha, max_iter, use_lead,
-                                    precision=precision, estimator=estimator)
+                                    precision=precision, estimator=estimator, osd_order=osd_order)
             fail_any = torch.zeros(n, dtype=torch.bool, device=self.device)
             logical = torch.zeros(n, dtype=torch.bool, device=self.device)
             nc = torch.zeros(n, dtype=torch.bool, device=self.device)

@@ -103,3 +103,16 @@ def test_one_slot_gives_the_same_result(codes, L):
     a = _run(L, code, oc, 0, 0.08, 40, 3, seed=9)
     b = _run(L, code, oc, 0, 0.08, 40, 3, seed=9, slots_ws=slot)
     assert torch.equal(a[4], b[4]) and torch.equal(a[5], b[5])
+
+
+def test_pipeline_with_osd_leaves_no_decoder_failures(codes, L):
+    """With OSD after min-sum every correction satisfies its syndrome, so every remaining failure
+    is a logical error; without OSD the same shots show decoder failures."""
+    from paper_2605_17796_gb300.pipeline import Pipeline
+    inst, code, oc = codes["PSL(2,7)"]
+    pipe = Pipeline(code, 4096, 0)
+    plain = pipe.run(L.NOISE_X, 0.03, 3000, seed=2)
+    with_osd = pipe.run(L.NOISE_X, 0.03, 3000, seed=2, osd_order=3)
+    assert plain.failures > plain.logical
+    assert with_osd.failures == with_osd.logical
+    assert with_osd.failures < plain.failures
