@@ -5,7 +5,7 @@
 Samples X noise, then times lead_decode (LEAD or, with --baseline, plain min-sum) and
 lead_local_estimate on the same syndromes, in the storage format of --precision (0 binary32,
 1 bfloat16, 2 binary16); with --priors also the per-qubit-prior path (priors drawn uniformly
-from [p/2, 3p/2]). Used for kernel tuning and for small ncu captures.
+from [p/2, 3p/2]); with --osd K also OSD-CS of order K on the shots min-sum leaves unconverged. Used for kernel tuning and for small ncu captures.
 """
 from __future__ import annotations
 
@@ -27,6 +27,7 @@ def main(argv=None):
     ap.add_argument("--skip-decode", action="store_true")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--priors", action="store_true")
+    ap.add_argument("--osd", type=int, default=None, help="also time OSD-CS of this order after decode")
     args = ap.parse_args(argv)
 
     import torch
@@ -71,6 +72,20 @@ def main(argv=None):
             nbytes = shots * (info.n * esize + info.words_m[0] * 4)
             print(f"local_estimate {args.code} {shots} shots precision {args.precision}: {ms:.3f} ms, "
                   f"{shots / ms * 1e3:.3e} shots/s, {nbytes / ms / 1e6:.1f} GB/s algorithmic")
+    if args.osd is not None:
+        post = torch.zeros((shots, info.n), dtype=torch.float32, device="cuda")
+        prior = torch.zeros((shots, info.n), dtype=torch.float32, device="cuda")
+        ows = torch.zeros(code.osd_workspace_bytes(o, shots) // 4 + 64, dtype=torch.int32, device="cuda")
+        for _ in range(args.reps):
+            code.decode(o, sz, shots, corr, st, it, llr=post, workspace=ws)
+            if not args.baseline:
+                code.local_estimate(lead.opts(side=0, p=args.p), sz, shots, prior, ws)
+            torch.cuda.synchronize()
+            todo = int(((st & lead.ST_CONVERGED) == 0).sum())
+            ms = timed(lambda: code.osd(o, args.osd, sz, shots, post, st, corr,
+                                        prior=None if args.baseline else prior, workspace=ows))
+            print(f"osd {args.code} order {args.osd}: {todo} of {shots} shots unconverged, {ms:.3f} ms, "
+                  f"{todo / ms * 1e3:.3e} post-processed shots/s")
     if args.priors:
         prior = torch.rand((shots, info.n), generator=torch.Generator(device="cuda").manual_seed(1),
                            device="cuda") * args.p + 0.5 * args.p
