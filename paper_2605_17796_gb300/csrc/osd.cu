@@ -255,20 +255,28 @@ __global__ void __launch_bounds__(kOsdThreads) osd_kernel(OsdArgs a, double p_ch
         }
         for (int kk = tid; kk < k; kk += bd) synq[kk] = synb[kphys[kk]];
         __syncthreads();
+        // warp per row, the row's mask bits walked once (warp-uniform), lanes on words lane and
+        // lane + 32 (a row has at most 64 words: n <= 4096); the row's words are loaded first so
+        // the loads are in flight during the walk
+        const bool has0 = lane < W, has1 = lane + 32 < W;
         for (int i = warp; i < m; i += nwarps) {
           const unsigned long long am = amask[i];
           if (!am) continue;
           unsigned long long* row = mat + (size_t)i * W;
-          for (int w = lane; w < W; w += 32) {
-            unsigned long long acc = 0ull;
-            for (unsigned long long r = am; r; r &= r - 1) acc ^= qrows[(__ffsll((long long)r) - 1) * W + w];
-            row[w] ^= acc;
+          const unsigned long long r0 = has0 ? row[lane] : 0ull;
+          const unsigned long long r1 = has1 ? row[lane + 32] : 0ull;
+          unsigned long long acc0 = 0ull, acc1 = 0ull;
+          unsigned int sacc = 0;
+          for (unsigned long long r = am; r; r &= r - 1) {
+            const int kk = __ffsll((long long)r) - 1;
+            const unsigned long long* q = qrows + kk * W;
+            if (has0) acc0 ^= q[lane];
+            if (has1) acc1 ^= q[lane + 32];
+            sacc ^= synq[kk];
           }
-          if (lane == 0) {
-            unsigned int sacc = 0;
-            for (unsigned long long r = am; r; r &= r - 1) sacc ^= synq[__ffsll((long long)r) - 1];
-            synb[i] ^= (uint8_t)sacc;
-          }
+          if (has0) row[lane] = r0 ^ acc0;
+          if (has1) row[lane + 32] = r1 ^ acc1;
+          if (lane == 0) synb[i] ^= (uint8_t)sacc;
         }
         __syncthreads();
       }
@@ -291,8 +299,14 @@ __global__ void __launch_bounds__(kOsdThreads) osd_kernel(OsdArgs a, double p_ch
       long long acc = Wc[c];
       const int wc = c >> 6;
       const unsigned long long bit = 1ull << (c & 63);
-      for (int i = 0; i < rank; ++i)
-        if (mat[(size_t)rowof[i] * W + wc] & bit) acc += dval[i];
+      for (int i0 = 0; i0 < rank; i0 += 8) {           // eight independent loads in flight
+        unsigned long long wv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) wv[u] = i0 + u < rank ? mat[(size_t)rowof[i0 + u] * W + wc] : 0ull;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (wv[u] & bit) acc += dval[i0 + u];
+      }
       const long long cost = cost0 + acc;
       if (cost < bc || (cost == bc && c < bi)) {
         bc = cost;
@@ -381,7 +395,7 @@ int lead_osd(const lead_code* code, const lead_decode_opts* opts, int32_t order,
   if (!opts || opts->side < 0 || opts->side > 1 || order < 0 || order > kOsdMaxOrder || shots < 0)
     return LEAD_EINVAL;
   const HostSide& hs = code->side[opts->side];
-  if (code->n > kOsdMaxN || hs.m > kOsdMaxM) return LEAD_EINVAL;
+  if (code->n > kOsdMaxN || hs.m > kOsdMaxM) return LEAD_EINVAL;     // rows of <= 64 words
   if (!prior && !(opts->p > 0.0 && opts->p < 0.5)) return LEAD_EINVAL;
   if (shots == 0) return LEAD_OK;
   if (!syn || !post || !status || !corr || !workspace || ((uintptr_t)workspace & 15)) return LEAD_EINVAL;
