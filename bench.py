@@ -261,7 +261,7 @@ def main():
     torch.cuda.set_device(local_rank)
     dev = local_rank
 
-    from paper_2605_17796_gb300 import lead
+    from paper_2605_17796_gb300 import lead, replicas
     from paper_2605_17796_gb300.pipeline import Pipeline
 
     inst = _instance()
@@ -291,7 +291,7 @@ def main():
     def step(step_idx):
         out = []
         for pi, p in enumerate(P_SWEEP):
-            off = ((step_idx * world + rank) * len(P_SWEEP) + pi) * args.shots_per_p
+            off = replicas.shot_offset(step_idx, rank, world, pi, len(P_SWEEP), args.shots_per_p)
             out.append(pipe.run(lead.NOISE_X, p, args.shots_per_p, seed=0, offset=off))
         return out
 
@@ -319,11 +319,12 @@ def main():
     if sampler:
         sampler.terminate()
         sampler.wait()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
+    elapsed_ms = replicas.max_over_ranks(ev0.elapsed_time(ev1), world, device="cuda")
+    # failure and iteration counts of the last timed sweep, over all ranks
+    counts = replicas.sum_over_ranks([r.failures for r in sweep] + [r.iters_sum for r in sweep] +
+                                     [r.shots for r in sweep], world, device="cuda")
+    n_p = len(P_SWEEP)
+    sweep_fail, sweep_iters, sweep_shots = counts[:n_p], counts[n_p:2 * n_p], counts[2 * n_p:]
     total_shots = args.steps * len(P_SWEEP) * args.shots_per_p * world
     value = total_shots / (elapsed_ms / 1e3)
 
@@ -414,7 +415,7 @@ def main():
         serving = _serving(lead, args.serving_rate, args.serving_requests, code)
 
     clocks = _clock_summary(clk_path, dev)
-    ler = {f"{p:.2f}": r.failures / r.shots for p, r in zip(P_SWEEP, sweep)}
+    ler = {f"{p:.2f}": f / n for p, f, n in zip(P_SWEEP, sweep_fail, sweep_shots)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -430,7 +431,7 @@ def main():
                                 if precision else None),
             "serving": serving,
             "clocks": clocks, "ler": ler,
-            "mean_iters": {f"{p:.2f}": r.iters_sum / r.shots for p, r in zip(P_SWEEP, sweep)}}
+            "mean_iters": {f"{p:.2f}": i / n for p, i, n in zip(P_SWEEP, sweep_iters, sweep_shots)}}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
