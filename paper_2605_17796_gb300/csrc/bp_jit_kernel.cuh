@@ -321,6 +321,14 @@ __device__ __forceinline__ void red_cluster_or(unsigned int addr, unsigned int v
   asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -426,25 +434,10 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
         if (bad) red_cluster_or(flag0 + 4u * (t & 1), 1u);
       }
       if (rank == 0 && tid == 0) flags[(t + 1) & 1] = 0u;
-      cluster_sync();
-      const bool conv = ld_cluster_u32(flag0 + 4u * (t & 1)) == 0u;
-      if (conv || t >= a.max_iter) {
-        if (lane_ok) {
-          for (int j = 0; j < NL; ++j) {
-            if (cluster_partner(a.pa, j, v, V).first) {
-              const int q = __ldg(a.views + v * NL + j);
-              if ((hm >> j) & 1) atomicOr(cb + (q >> 5), 1u << (q & 31));
-              if (a.llr) a.llr[g0 * a.n + q] = dec(Ps[j * TS + tid]);
-            }
-          }
-        }
-        if (rank == 0 && tid == 0) {
-          a.status[g0] = conv ? (unsigned char)1 : (unsigned char)2;
-          if (a.iters) a.iters[g0] = t;
-        }
-        break;                  // uniform across the cluster: every thread read the same flag
-      }
-      if (lane_ok) {
+      cluster_arrive();
+      // the check-node update reads only this thread's own posteriors: computed between the
+      // barrier's arrive and its wait, it hides the barrier (discarded if the shot stops here)
+      if (lane_ok && t < a.max_iter) {
 #pragma unroll
         for (int r = 0; r < ML; ++r) {
           const float m1o = mag[r].m1(), m2o = mag[r].m2();
@@ -471,6 +464,26 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
           mag[r].set(n1, n2);
           meta[r] = sg | ((unsigned int)am << 26) | (par << 31);
         }
+      }
+      cluster_wait();
+      const bool conv = ld_cluster_u32(flag0 + 4u * (t & 1)) == 0u;
+      if (conv || t >= a.max_iter) {
+        if (lane_ok) {
+          for (int j = 0; j < NL; ++j) {
+            if (cluster_partner(a.pa, j, v, V).first) {
+              const int q = __ldg(a.views + v * NL + j);
+              if ((hm >> j) & 1) atomicOr(cb + (q >> 5), 1u << (q & 31));
+              if (a.llr) a.llr[g0 * a.n + q] = dec(Ps[j * TS + tid]);
+            }
+          }
+        }
+        if (rank == 0 && tid == 0) {
+          a.status[g0] = conv ? (unsigned char)1 : (unsigned char)2;
+          if (a.iters) a.iters[g0] = t;
+        }
+        break;                  // uniform across the cluster: every thread read the same flag
+      }
+      if (lane_ok) {
         // U of every slot: its rows' new messages summed in increasing row order (binary32, the
         // first term stored as is: 0 + c == c), then stored once
 #pragma unroll
