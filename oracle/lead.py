@@ -13,7 +13,7 @@ Phase 2 (regularisation): every qubit lies in exactly two views of a side (|S_i|
 p_i = alpha * (q_{v0,j0} + q_{v1,j1}) / 2.  The prior LLR is ln((1 - p_i)/p_i) with p_i clamped
 to [2^-23, 1 - 2^-23] (the paper does not state a clamp; this one keeps binary32 finite).
 Phase 3 (global decoder): flooding min-sum with scaling 1 and at most ``max_iter`` iterations
-(the paper's BP-OSD global decoder is replaced by its BP part; OSD is not built).
+(the BP part of the paper's BP-OSD global decoder; OSD-CS post-processing is in ``osd``).
 
 Two numeric tracks:
 * ``prior_f64``: q, p_i and the LLR in FP64 -- the quantities the single-precision path must
@@ -286,6 +286,44 @@ def decode(code: TannerCode, side_id: int, syn: np.ndarray, p: float, alpha: flo
         lam = channel_prior_f32(code.n, syn.shape[0], p)
     side = code.sides[side_id]
     return min_sum(side.H, side.m_l, syn, lam, max_iter, precision=precision)
+
+
+def redecode(code: TannerCode, side_id: int, syn: np.ndarray, post: np.ndarray, alpha: float = 1.0,
+             max_iter: int = 32, use_lead: bool = True, precision: int = PREC_FP32):
+    """One round of iterated LEAD (an extension; the paper runs Algorithm 1 once): the per-qubit
+    prior is the flip probability the last global posterior LLR states, p_i = 1 / (1 + e^{post_i})
+    (``local.sigmoid_f32``), clamped to [2^-23, 1 - 2^-23]; then Algorithm 1 with that prior:
+    Phase 1 the exact local posterior under the product prior with its least-cost decision and
+    boost (``local_priors``), Phase 2 ``merge_priors_f32``, Phase 3 ``min_sum``. use_lead=False
+    hands lambda(p_i) to min-sum directly. Returns (corr, status, iters, post) as ``decode``."""
+    prior = np.clip(local.sigmoid_f32(post), local.P_MIN_F, local.P_MAX_F).astype(np.float32)
+    if use_lead:
+        q, _ = local_priors(code, side_id, syn, prior)
+        lam = merge_priors_f32(code, side_id, q, alpha)
+    else:
+        lam = local.llr_f32(prior)
+    side = code.sides[side_id]
+    return min_sum(side.H, side.m_l, syn, lam, max_iter, precision=precision)
+
+
+def decode_iterated(code: TannerCode, side_id: int, syn: np.ndarray, p: float, rounds: int, alpha: float = 1.0,
+                    max_iter: int = 32, use_lead: bool = True, precision: int = PREC_FP32,
+                    estimator: int = EST_EXACT):
+    """Iterated LEAD: round 0 is ``decode``; each further round applies ``redecode`` to the shots
+    whose status lacks STATUS_CONVERGED, with their last posteriors. Converged shots keep their
+    round's result, and iterations add up over the rounds a shot ran. Returns (corr, status,
+    iters, post) as ``decode``."""
+    corr, st, it, post = decode(code, side_id, syn, p, alpha, max_iter, use_lead, precision, estimator)
+    for _ in range(1, rounds):
+        sel = np.nonzero((st & STATUS_CONVERGED) == 0)[0]
+        if sel.size == 0:
+            break
+        c, s, i, pst = redecode(code, side_id, syn[sel], post[sel], alpha, max_iter, use_lead, precision)
+        corr[sel] = c
+        st[sel] = s
+        it[sel] += i
+        post[sel] = pst
+    return corr, st, it, post
 
 
 def check(code: TannerCode, side_id: int, err: np.ndarray, corr: np.ndarray) -> np.ndarray:
