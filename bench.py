@@ -226,6 +226,29 @@ def _precision_modes(lead, pipe, shots: int, p: float = 0.05):
     return out
 
 
+def _iterated_lead(lead, pipe, shots: int, ps=(0.02, 0.03), rounds=(1, 2, 3)):
+    """Iterated LEAD (an extension: further rounds on the unconverged shots, the last global
+    posterior as per-qubit prior): logical error rate, mean global iterations summed over rounds,
+    and decode throughput per (p, rounds) on the same shots."""
+    import torch
+    out = []
+    for p in ps:
+        for R in rounds:
+            pipe.run(lead.NOISE_X, p, min(shots, 4096), seed=9, offset=0, rounds=R)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = pipe.run(lead.NOISE_X, p, shots, seed=9, offset=0, rounds=R)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out.append({"p": p, "rounds": R, "shots_per_s": shots / (ms / 1e3), "ler": r.failures / shots,
+                        "ler_ci95": wilson95(r.failures, shots), "mean_iters": r.iters_sum / shots,
+                        "not_converged": r.not_converged / shots})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -242,6 +265,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--precision-shots", type=int, default=1_000_000)
     ap.add_argument("--no-modes", action="store_true")
+    ap.add_argument("--iterated-shots", type=int, default=1 << 18)
     args = ap.parse_args()
 
     if args.oracle_child:
@@ -433,10 +457,11 @@ def main():
                "sample": f"{procs} single-threaded numpy processes x {args.oracle_shots_per_p} shots per p "
                          f"x 10 p values on disjoint shots ({r['shots']} shots, {r['seconds']:.1f} s wall)"}
 
-    local_est = precision = None
+    local_est = precision = iterated = None
     if not args.no_modes and world == 1:
         local_est = _local_estimation(lead, code, pipe, peaks["hbm_gbs"], min(args.chunk, 1 << 20))
         precision = _precision_modes(lead, pipe, args.precision_shots)
+        iterated = _iterated_lead(lead, pipe, min(args.iterated_shots, args.chunk))
 
     serving = None
     if not args.no_serving and world == 1:
@@ -457,6 +482,8 @@ def main():
             "local_estimation": local_est,
             "precision_modes": ({"p": 0.05, "shots": args.precision_shots, "modes": precision}
                                 if precision else None),
+            "iterated_lead": ({"shots": min(args.iterated_shots, args.chunk), "runs": iterated}
+                              if iterated else None),
             "serving": serving,
             "clocks": clocks, "ler": ler,
             "mean_iters": {f"{p:.2f}": i / n for p, i, n in zip(P_SWEEP, sweep_iters, sweep_shots)}}

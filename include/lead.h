@@ -342,6 +342,32 @@ int lead_decode_priors(const lead_code* code, const lead_decode_opts* opts, cons
                        void* workspace, size_t ws_bytes, void* stream);
 
 /*
+ * lead_decode_iterated -- iterated LEAD, an extension: the paper runs Algorithm 1 once. Round 0
+ * is lead_decode. Each further round takes the shots whose status lacks LEAD_ST_CONVERGED,
+ * turns every qubit's last global posterior LLR post_i into a per-qubit prior
+ * p_i = 1 / (1 + e^{post_i}) (post clamped to [-88, 88]; the exponential in binary64 by
+ * Cody-Waite reduction and its Taylor series through degree 14, one rounding to binary32), and
+ * decodes those shots again as lead_decode_priors does with that prior: the exact local
+ * posterior under the product prior with use_lead == 1 (opts->estimator applies to round 0
+ * only), the prior LLR alone with use_lead == 0. Shots that converged keep their result.
+ *  rounds 1..64 (1 = lead_decode); stops early when every shot has converged.
+ *  corr, status: those of the last round a shot ran; iters (nullable): global iterations summed
+ *  over the rounds a shot ran; llr (dev, shots x n float): the posterior LLRs, required when
+ *  rounds > 1 (they carry the prior from round to round).
+ *  workspace (dev, 256-byte aligned) >= lead_iterated_workspace_bytes(opts, shots): the
+ *  decoders' own workspace plus the compacted batch, about (4 n + 4 words_m + 4 words_n + 9)
+ *  bytes per shot more.
+ *  Between rounds the call copies the number of unconverged shots to the host and waits for the
+ *  stream: with rounds > 1 it synchronises, so it cannot be captured in a CUDA graph.
+ * Errors: those of lead_decode and lead_decode_priors (checked before round 0 when rounds > 1),
+ *         LEAD_EINVAL for rounds outside 1..64, shots > 2^31 - 1 or llr NULL with rounds > 1.
+ */
+size_t lead_iterated_workspace_bytes(const lead_code* code, const lead_decode_opts* opts, int64_t shots);
+int lead_decode_iterated(const lead_code* code, const lead_decode_opts* opts, int32_t rounds, const uint32_t* syn,
+                         int64_t shots, uint32_t* corr, uint8_t* status, int32_t* iters, float* llr,
+                         void* workspace, size_t ws_bytes, void* stream);
+
+/*
  * lead_osd -- ordered-statistics post-processing (OSD-CS) of the shots whose min-sum did not
  * converge (status without LEAD_ST_CONVERGED); the paper's global decoder is BP-OSD in the
  * osd_cs mode of order 3 (Sec. IV-A). Per such shot, on side opts->side:

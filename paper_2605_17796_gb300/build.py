@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "liblead.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["device.cu", "sample.cu", "decode.cu", "priors.cu", "local.cu", "osd.cu"]
+CU_SOURCES = ["device.cu", "sample.cu", "decode.cu", "priors.cu", "local.cu", "osd.cu", "iterated.cu"]
 CPP_SOURCES = ["code.cpp", "jit.cpp", "server.cpp"]
 # the run-time specialised min-sum kernel: these files are embedded (in this order) as text
 JIT_SOURCES = ["bp_jit_args.h", "lead_math.cuh", "bp_jit_kernel.cuh"]

@@ -123,31 +123,6 @@ __global__ void table_kernel(int nl, int m_l, double r, const int32_t* __restric
   }
 }
 
-// e^x for binary64 x in [-88, 88]: Cody-Waite reduction k = rint(x / ln 2), r = (x - k LN2_HI) -
-// k LN2_LO with the fdlibm split of ln 2 (LN2_HI has 21 trailing zero bits, so k LN2_HI is exact),
-// e^r by its Taylor series through r^14 in Horner form, times 2^k (exact). Separate
-// round-to-nearest binary64 operations throughout.
-__device__ __forceinline__ double exp_series_f64(double x) {
-  const double kInvLn2 = __longlong_as_double(0x3FF71547652B82FEll);
-  const double kLn2Hi = __longlong_as_double(0x3FE62E42FEE00000ll);
-  const double kLn2Lo = __longlong_as_double(0x3DEA39EF35793C76ll);
-  constexpr double kInvFact[15] = {1.0 / 1.0, 1.0 / 1.0, 1.0 / 2.0, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0,
-                                   1.0 / 720.0, 1.0 / 5040.0, 1.0 / 40320.0, 1.0 / 362880.0,
-                                   1.0 / 3628800.0, 1.0 / 39916800.0, 1.0 / 479001600.0,
-                                   1.0 / 6227020800.0, 1.0 / 87178291200.0};
-  const double k = rint(__dmul_rn(x, kInvLn2));
-  const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(k, kLn2Hi)), __dmul_rn(k, kLn2Lo));
-  double s = kInvFact[14];
-  for (int n = 13; n >= 0; --n) s = __dadd_rn(__dmul_rn(s, r), kInvFact[n]);
-  return ldexp(s, (int)k);
-}
-
-// q = 1 / (1 + e^post) in binary32 from a binary32 posterior LLR (clamped to [-88, 88]).
-__device__ __forceinline__ float sigmoid_f32(float post) {
-  const double x = (double)fminf(fmaxf(post, -88.0f), 88.0f);
-  return __double2float_rn(__ddiv_rn(1.0, __dadd_rn(1.0, exp_series_f64(x))));
-}
-
 __global__ void fill_i32_kernel(int32_t* __restrict__ out, int n, int32_t value) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = value;
 }

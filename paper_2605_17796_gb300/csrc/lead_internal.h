@@ -91,6 +91,7 @@ int prepare_device(lead_code* code, int device);
 void release_device(lead_code* code);
 int bp_shots_per_block(const lead_code* code);   // shots per CTA of the min-sum kernel
 size_t decode_workspace_bytes(const lead_code* code, int side);   // what lead_decode reads
+int priors_check(const lead_code* code, const lead_decode_opts* o);   // lead_decode_priors' argument checks
 struct BPJitArgs;
 struct Geometry {               // launch geometry of the min-sum kernel for one side
   int spb, cluster, ts, block, minblocks;

@@ -342,6 +342,23 @@ int validate(const lead_code* code, const lead_decode_opts* o) {
 }
 
 }  // namespace
+
+// The checks lead_decode_priors makes before any device work: device, options and, with the
+// local stage, a local code the per-qubit kernel serves.
+int priors_check(const lead_code* code, const lead_decode_opts* o) {
+  int rc = check_device(code);
+  if (rc != LEAD_OK) return rc;
+  rc = validate(code, o);
+  if (rc != LEAD_OK || !o->use_lead) return rc;
+  const HostSide& hs = code->side[o->side];
+  const DeviceSide& ds = code->dside[o->side];
+  if (!ds.xcls || !ds.cbase || !ds.ckern) return LEAD_EINVAL;
+  const size_t nk = hs.ckern.size();
+  const bool ok = (code->delta == 6 && hs.kRB == 3 && hs.m_l == 9 && nk == 512) ||
+                  (code->delta == 4 && hs.kRB == 2 && hs.m_l == 4 && nk == 16);
+  return ok ? LEAD_OK : LEAD_EINVAL;
+}
+
 }  // namespace lead
 
 extern "C" {

@@ -93,6 +93,12 @@ EXPORTS = {
                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                           ctypes.c_void_p]),
+    "lead_iterated_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts),
+                                                        ctypes.c_int64]),
+    "lead_decode_iterated": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_int32,
+                                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                            ctypes.c_void_p]),
     "lead_osd_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_int64]),
     "lead_osd": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_int32, ctypes.c_void_p,
                                 ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -300,6 +306,19 @@ class Code:
         nb = workspace.numel() * workspace.element_size() if workspace is not None else 0
         _check("lead_decode_priors", LIB.lead_decode_priors(
             self._h, ctypes.byref(opts), _ptr(syn), shots, _ptr(prior), _ptr(corr), _ptr(status), _ptr(iters),
+            _ptr(llr), ws, nb, _stream(stream)))
+
+    def iterated_workspace_bytes(self, opts: LeadDecodeOpts, shots: int) -> int:
+        return int(LIB.lead_iterated_workspace_bytes(self._h, ctypes.byref(opts), shots))
+
+    def decode_iterated(self, opts: LeadDecodeOpts, rounds: int, syn, shots: int, corr, status, iters=None,
+                        llr=None, workspace=None, stream=None):
+        """lead_decode_iterated: Algorithm 1, then up to rounds - 1 more rounds on the unconverged
+        shots with the last posterior as per-qubit prior (an extension of the paper)."""
+        ws = _ptr(workspace)
+        nb = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        _check("lead_decode_iterated", LIB.lead_decode_iterated(
+            self._h, ctypes.byref(opts), rounds, _ptr(syn), shots, _ptr(corr), _ptr(status), _ptr(iters),
             _ptr(llr), ws, nb, _stream(stream)))
 
     def osd_workspace_bytes(self, opts: LeadDecodeOpts, shots: int) -> int:

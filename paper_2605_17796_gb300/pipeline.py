@@ -41,6 +41,7 @@ class Pipeline:
         ws = max(code.workspace_bytes(lead.opts(side=s, use_lead=True)) for s in range(2))
         self.workspace = torch.zeros(max(ws, 256) // 4 + 64, dtype=torch.int32, **kw)
         self._osd = None          # posterior / prior / workspace buffers, made on first OSD use
+        self._iter = None         # posterior / workspace buffers of iterated LEAD, made on first use
 
     def _osd_buffers(self):
         if self._osd is None:
@@ -52,14 +53,26 @@ class Pipeline:
                          "ws": torch.zeros(nb // 4 + 64, dtype=torch.int32, **kw)}
         return self._osd
 
+    def _iter_buffers(self):
+        if self._iter is None:
+            kw = dict(device=self.device)
+            nb = max(self.code.iterated_workspace_bytes(lead.opts(side=s), self.chunk) for s in range(2))
+            self._iter = {"post": torch.zeros((self.chunk, self.code.info.n), dtype=torch.float32, **kw),
+                          "ws": torch.zeros(nb // 4 + 64, dtype=torch.int32, **kw)}
+        return self._iter
+
     def sides_for(self, noise: int):
         return {lead.NOISE_X: [0], lead.NOISE_Z: [1], lead.NOISE_DEPOL: [0, 1]}[noise]
 
     def chunk_step(self, noise: int, p: float, shots: int, seed: int, offset: int, alpha: float = 1.0,
                    max_iter: int = 32, use_lead: bool = True, with_check: bool = True,
-                   precision: int = lead.PREC_FP32, estimator: int = lead.EST_EXACT, osd_order=None):
+                   precision: int = lead.PREC_FP32, estimator: int = lead.EST_EXACT, osd_order=None,
+                   rounds: int = 1):
         """One chunk (shots <= chunk): sample, decode the sides the noise touches (with OSD-CS of
-        osd_order on the shots min-sum leaves unconverged, when given), check."""
+        osd_order on the shots min-sum leaves unconverged, when given; with rounds > 1, iterated
+        LEAD instead of one pass of Algorithm 1), check."""
+        if rounds > 1 and osd_order is not None:
+            raise ValueError("iterated LEAD and OSD post-processing are not combined")
         c = self.code
         sides = self.sides_for(noise)
         c.sample(noise, p, shots, seed, offset,
@@ -69,7 +82,11 @@ class Pipeline:
         for s in sides:
             o = lead.opts(side=s, p=p_side, alpha=alpha, max_iter=max_iter, use_lead=use_lead, precision=precision,
                           estimator=estimator)
-            if osd_order is None:
+            if rounds > 1:
+                b = self._iter_buffers()
+                c.decode_iterated(o, rounds, self.syn[s], shots, self.corr[s], self.status[s], self.iters[s],
+                                  llr=b["post"][:shots], workspace=b["ws"])
+            elif osd_order is None:
                 c.decode(o, self.syn[s], shots, self.corr[s], self.status[s], self.iters[s],
                          workspace=self.workspace)
             else:
@@ -89,14 +106,15 @@ class Pipeline:
 
     def run(self, noise: int, p: float, shots: int, seed: int = 0, offset: int = 0, alpha: float = 1.0,
             max_iter: int = 32, use_lead: bool = True, precision: int = lead.PREC_FP32,
-            estimator: int = lead.EST_EXACT, osd_order=None) -> RunResult:
+            estimator: int = lead.EST_EXACT, osd_order=None, rounds: int = 1) -> RunResult:
         """Decode `shots` shots in chunks and return failure / iteration counts."""
         acc = None
         done = 0
         while done < shots:
             n = min(self.chunk, shots - done)
             sides = self.chunk_step(noise, p, n, seed, offset + done, alpha, max_iter, use_lead,
-                                    precision=precision, estimator=estimator, osd_order=osd_order)
+                                    precision=precision, estimator=estimator, osd_order=osd_order,
+                                    rounds=rounds)
             fail_any = torch.zeros(n, dtype=torch.bool, device=self.device)
             logical = torch.zeros(n, dtype=torch.bool, device=self.device)
             nc = torch.zeros(n, dtype=torch.bool, device=self.device)

@@ -9,7 +9,10 @@ converge, and the mean global iterations. One line per p is added for the standa
 baseline (alpha = null) on the same shots. Sec. IV-C's experiment is alpha = 1 against
 alpha = 0.01 across the noise range. --estimator minsum uses local min-sum BP as the Phase-1
 local decoder instead of the exact posterior; --osd ORDER adds OSD-CS of that order after
-min-sum (the paper's BP-OSD global decoder), for LEAD and the baseline alike.
+min-sum (the paper's BP-OSD global decoder), for LEAD and the baseline alike. --rounds R > 1
+runs iterated LEAD (an extension): up to R - 1 further rounds on the unconverged shots, each
+with the last global posterior as per-qubit prior; for the baseline the same rounds restart
+min-sum from that prior without the local stage.
 
 The normalised iteration count of Sec. IV-A, I = I_g + I_l m_l / m_g, is reported with I_l
 summed over the |G| parallel local decoders of a shot (m_g = |G| m_l), i.e. I_l m_l / m_g is
@@ -54,7 +57,7 @@ def expected_local_iterations(code: lead.Code, side: int, p: float, estimator: i
 
 def sweep(code: lead.Code, ps, alphas, shots: int, noise: int = lead.NOISE_X, precision: int = lead.PREC_FP32,
           chunk: int = 1 << 18, seed: int = 0, baseline: bool = True, estimator: int = lead.EST_EXACT,
-          osd_order=None):
+          osd_order=None, rounds: int = 1):
     """Yields one result dict per (alpha, p) and, with baseline, per p for plain min-sum."""
     pipe = Pipeline(code, min(chunk, shots), code.info.prepared_device)
     configs = [(a, True) for a in alphas] + ([(None, False)] if baseline else [])
@@ -62,13 +65,13 @@ def sweep(code: lead.Code, ps, alphas, shots: int, noise: int = lead.NOISE_X, pr
         il = expected_local_iterations(code, 0, p, estimator) if noise == lead.NOISE_X else None
         for alpha, use_lead in configs:
             r = pipe.run(noise, p, shots, seed=seed, offset=0, alpha=alpha if alpha else 1.0, use_lead=use_lead,
-                         precision=precision, estimator=estimator, osd_order=osd_order)
+                         precision=precision, estimator=estimator, osd_order=osd_order, rounds=rounds)
             ig = r.iters_sum / shots
             row = {"p": p, "alpha": alpha, "decoder": "LEAD" if use_lead else "min-sum", "shots": shots,
                    "ler": r.failures / shots, "ler_ci95": wilson95(r.failures, shots),
                    "not_converged": r.not_converged / shots, "mean_iters": ig, "precision": precision,
                    "estimator": ("minsum" if estimator == lead.EST_MINSUM else "exact") if use_lead else None,
-                   "osd_order": osd_order}
+                   "osd_order": osd_order, "rounds": rounds}
             if use_lead and il is not None:
                 row["local_iters_per_vertex"] = il
                 row["normalized_iters"] = ig + il
@@ -88,6 +91,7 @@ def main(argv=None):
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--estimator", choices=["exact", "minsum"], default="exact")
     ap.add_argument("--osd", type=int, default=None)
+    ap.add_argument("--rounds", type=int, default=1)
     ap.add_argument("--chunk", type=int, default=1 << 16)
     args = ap.parse_args(argv)
     code = lead.Code.from_instance(workloads.standard(args.code, 0)).prepare(0)
@@ -96,7 +100,7 @@ def main(argv=None):
     alphas = [float(x) for x in args.alpha.split(",")]
     est = lead.EST_MINSUM if args.estimator == "minsum" else lead.EST_EXACT
     for row in sweep(code, ps, alphas, args.shots, noise, args.precision, chunk=args.chunk,
-                     baseline=not args.no_baseline, estimator=est, osd_order=args.osd):
+                     baseline=not args.no_baseline, estimator=est, osd_order=args.osd, rounds=args.rounds):
         row["code"] = args.code
         row["noise"] = args.noise
         print(json.dumps(row), flush=True)

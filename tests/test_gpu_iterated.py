@@ -1,0 +1,272 @@
+"""Iterated LEAD (lead_decode_iterated) against the oracle.
+
+Bar: bit-exact wherever the arithmetic is fixed, stage by stage:
+* one round is lead_decode, bit for bit;
+* every further round equals lead_decode_priors on the unconverged shots with the prior
+  clip(sigmoid_f32(post)) that the oracle computes from the previous round's posterior: so the
+  conversion and the compaction are bit-exact, and the scatter keeps converged shots untouched;
+* that round's global min-sum equals the oracle's min_sum on the merged prior LLRs the kernel
+  computes from the same priors (corrections, status, iterations, posteriors), and on SL(2,3)
+  the local least-cost decisions equal the oracle's;
+* the local posteriors themselves carry the per-qubit path's tolerance (relative 1e-4, in
+  test_gpu_priors), so the whole chain against the oracle's FP64 posteriors is compared on the
+  outcome: most re-decoded shots end identically, and the shots on which only one side fails
+  split evenly between the two (a sign test).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import lead as olead
+from oracle import local as olocal
+from oracle import philox, tanner
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2605_17796_gb300 import lead
+    return lead
+
+
+@pytest.fixture(scope="module")
+def codes(L):
+    out = {}
+    for name in ("SL(2,3)", "PSL(2,7)", "PSL(2,11)"):
+        inst = workloads.standard(name, 0)
+        out[name] = (inst, L.Code.from_instance(inst).prepare(0), tanner.from_instance(inst))
+    return out
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _syn_dev(code, side, syn):
+    return _dev(philox.pack_bits(syn, code.info.words_m[side]).view(np.int32))
+
+
+def _out(code, shots):
+    info = code.info
+    return (torch.full((shots, info.words_n), -1, dtype=torch.int32, device="cuda"),
+            torch.zeros(shots, dtype=torch.uint8, device="cuda"),
+            torch.full((shots,), -1, dtype=torch.int32, device="cuda"),
+            torch.zeros((shots, info.n), dtype=torch.float32, device="cuda"))
+
+
+def _host(corr, st, it, post):
+    torch.cuda.synchronize()
+    return corr.cpu().numpy(), st.cpu().numpy(), it.cpu().numpy(), post.cpu().numpy()
+
+
+def _iterated(L, code, o, rounds, syn_d, shots):
+    corr, st, it, post = _out(code, shots)
+    ws = torch.empty(code.iterated_workspace_bytes(o, shots) + 256, dtype=torch.uint8, device="cuda")
+    code.decode_iterated(o, rounds, syn_d, shots, corr, st, it, post, ws)
+    return _host(corr, st, it, post)
+
+
+def _decode(L, code, o, syn_d, shots):
+    corr, st, it, post = _out(code, shots)
+    ws = torch.empty(code.workspace_bytes(o, shots) + 256, dtype=torch.uint8, device="cuda")
+    code.decode(o, syn_d, shots, corr, st, it, post, ws)
+    return _host(corr, st, it, post)
+
+
+def _decode_priors(L, code, o, syn_d, shots, prior):
+    corr, st, it, post = _out(code, shots)
+    ws = torch.empty(code.priors_workspace_bytes(o, shots) + 256, dtype=torch.uint8, device="cuda")
+    code.decode_priors(o, syn_d, shots, _dev(prior), corr, st, it, post, ws)
+    return _host(corr, st, it, post)
+
+
+def _merged_llr(L, code, o, syn_d, shots, prior):
+    info = code.info
+    llr = torch.zeros((shots, info.n), dtype=torch.float32, device="cuda")
+    ml = torch.zeros((shots, info.order), dtype=torch.int64, device="cuda")
+    ws = torch.empty(code.priors_workspace_bytes(o, shots) + 256, dtype=torch.uint8, device="cuda")
+    code.local_estimate_priors(o, syn_d, shots, _dev(prior), llr, ml=ml, workspace=ws)
+    torch.cuda.synchronize()
+    return llr.cpu().numpy(), ml.cpu().numpy().view(np.uint64).astype(np.int64)
+
+
+def _prior_of(post):
+    return np.clip(olocal.sigmoid_f32(post), olocal.P_MIN_F, olocal.P_MAX_F).astype(np.float32)
+
+
+def _same(a, b):
+    return all((x.view(np.uint8) == y.view(np.uint8)).all() for x, y in zip(a, b))
+
+
+def _errors(oc, side, p, shots, seed):
+    noise = philox.NOISE_X if side == 0 else philox.NOISE_Z
+    x, z = philox.sample_errors(noise, p, seed, np.arange(shots), oc.n)
+    e = x if side == 0 else z
+    return e, philox.syndromes(oc.sides[side].H, e)
+
+
+@pytest.mark.parametrize("name,side,p,shots", [("SL(2,3)", 0, 0.06, 100), ("PSL(2,7)", 1, 0.03, 64)])
+def test_one_round_is_decode(codes, L, name, side, p, shots):
+    inst, code, oc = codes[name]
+    _, syn = _errors(oc, side, p, shots, seed=2)
+    o = L.opts(side=side, p=p)
+    syn_d = _syn_dev(code, side, syn)
+    assert _same(_iterated(L, code, o, 1, syn_d, shots), _decode(L, code, o, syn_d, shots))
+    # llr may be NULL with one round
+    corr, st, it, _ = _out(code, shots)
+    ws = torch.empty(code.iterated_workspace_bytes(o, shots), dtype=torch.uint8, device="cuda")
+    code.decode_iterated(o, 1, syn_d, shots, corr, st, it, None, ws)
+    want = _decode(L, code, o, syn_d, shots)
+    assert _same(_host(corr, st, it, torch.zeros(1, device="cuda"))[:3], want[:3])
+
+
+CASES = [
+    # name, side, p, shots, rounds, use_lead, precision, estimator, oracle-checked rows
+    ("SL(2,3)", 0, 0.08, 200, 3, True, 0, 0, 200),
+    ("SL(2,3)", 1, 0.08, 150, 2, False, 0, 0, 150),
+    ("SL(2,3)", 0, 0.07, 120, 2, True, 1, 0, 120),
+    ("PSL(2,7)", 0, 0.03, 300, 3, True, 0, 0, 24),
+    ("PSL(2,7)", 1, 0.03, 200, 2, True, 2, 0, 16),
+    ("PSL(2,7)", 0, 0.02, 200, 2, True, 0, 1, 16),
+    ("PSL(2,11)", 0, 0.02, 48, 2, True, 0, 0, 4),
+]
+
+
+@pytest.mark.parametrize("name,side,p,shots,rounds,use_lead,precision,estimator,checked", CASES)
+def test_rounds_stage_by_stage(codes, L, name, side, p, shots, rounds, use_lead, precision, estimator, checked):
+    inst, code, oc = codes[name]
+    e, syn = _errors(oc, side, p, shots, seed=21)
+    syn_d = _syn_dev(code, side, syn)
+    o = L.opts(side=side, p=p, use_lead=use_lead, precision=precision, estimator=estimator)
+    po = L.opts(side=side, p=p, use_lead=use_lead, precision=precision)
+    got = _iterated(L, code, o, rounds, syn_d, shots)
+
+    # round 0 against the oracle's Algorithm 1 (a few rows; its own parity is tested elsewhere)
+    corr, st, it, post = _decode(L, code, o, syn_d, shots)
+    k = min(shots, 8)
+    wc, wst, wit, wpost = olead.decode(oc, side, syn[:k], p, use_lead=use_lead, precision=precision,
+                                       estimator=estimator)
+    assert (philox.unpack_bits(corr[:k].view(np.uint32), oc.n) == wc).all()
+    assert (st[:k] == wst).all() and (it[:k] == wit).all()
+    assert (post[:k].view(np.uint32) == wpost.view(np.uint32)).all()
+
+    H = oc.sides[side].H
+    redecoded = 0
+    for r in range(1, rounds):
+        sel = np.nonzero((st & L.ST_CONVERGED) == 0)[0]
+        if sel.size == 0:
+            break
+        prior = _prior_of(post[sel])
+        sel_d = _syn_dev(code, side, syn[sel])
+        c, s, i, pst = _decode_priors(L, code, po, sel_d, sel.size, prior)
+        if r == 1:
+            # the round's min-sum against the oracle, on the merged LLRs of the same priors
+            m = min(sel.size, checked)
+            if use_lead:
+                lam, ml = _merged_llr(L, code, po, _syn_dev(code, side, syn[sel[:m]]), m, prior[:m])
+                if name == "SL(2,3)":
+                    _, want_ml = olead.local_priors(oc, side, syn[sel[:m]], prior[:m])
+                    assert (ml == want_ml).all()
+            else:
+                lam = olocal.llr_f32(prior[:m])
+            wc, wst, wit, wpost = olead.min_sum(H, oc.sides[side].m_l, syn[sel[:m]], lam, 32, precision=precision)
+            assert (philox.unpack_bits(c[:m].view(np.uint32), oc.n) == wc).all()
+            assert (s[:m] == wst).all() and (i[:m] == wit).all()
+            assert (pst[:m].view(np.uint32) == wpost.view(np.uint32)).all()
+            redecoded = sel.size
+        corr[sel], st[sel], it[sel], post[sel] = c, s, it[sel] + i, pst
+    assert redecoded > 0
+    assert _same(got, (corr, st, it, post))
+    conv = (got[1] & L.ST_CONVERGED) != 0
+    assert (philox.syndromes(H, philox.unpack_bits(got[0].view(np.uint32), oc.n))[conv] == syn[conv]).all()
+
+
+def test_whole_chain_against_oracle(codes, L):
+    """SL(2,3): oracle iterated LEAD (FP64 local posteriors) against the kernel on the outcome.
+    Round 0 is bit-exact. The re-decoded shots are the ones whose min-sum failed to settle, and
+    there the kernel's binary32 posteriors (relative error up to 1e-4, so prior LLRs that differ
+    in their last bits) can steer min-sum elsewhere; neither side may be the better decoder, so
+    the shots on which exactly one of them fails must split evenly (a sign test at 3 sigma), and
+    most re-decoded shots end identically."""
+    inst, code, oc = codes["SL(2,3)"]
+    p, shots = 0.08, 600
+    e, syn = _errors(oc, 0, p, shots, seed=33)
+    o = L.opts(side=0, p=p)
+    corr, st, it, post = _iterated(L, code, o, 2, _syn_dev(code, 0, syn), shots)
+    wc, wst, wit, _ = olead.decode_iterated(oc, 0, syn, p, rounds=2)
+    c0 = olead.decode(oc, 0, syn, p)[1] == olead.STATUS_CONVERGED
+    redo = ~c0
+    assert redo.sum() > 60
+    gc = philox.unpack_bits(corr.view(np.uint32), oc.n)
+    assert (gc[c0] == wc[c0]).all() and (st[c0] == wst[c0]).all() and (it[c0] == wit[c0]).all()
+    same = (gc[redo] == wc[redo]).all(axis=1) & (st[redo] == wst[redo])
+    assert same.mean() >= 0.6
+    fail_gpu = olead.check(oc, 0, e, gc) != 0
+    fail_orc = olead.check(oc, 0, e, wc) != 0
+    only_gpu = int((fail_gpu & ~fail_orc).sum())
+    only_orc = int((fail_orc & ~fail_gpu).sum())
+    assert abs(only_gpu - only_orc) <= 3.0 * np.sqrt(only_gpu + only_orc) + 1
+
+
+def test_full_size_batch_rows(codes, L):
+    """PSL(2,7), p = 0.03, 2^18 shots, two rounds (the benchmark's configuration): sampled rows,
+    converged and re-decoded, around 1024-shot compaction blocks and the ragged end, equal the
+    same rows decoded alone; two re-decoded rows match the oracle's min-sum on the kernel's
+    merged LLRs."""
+    inst, code, oc = codes["PSL(2,7)"]
+    info = code.info
+    shots, p = 1 << 18, 0.03
+    err = torch.zeros((shots, info.words_n), dtype=torch.int32, device="cuda")
+    syn_d = torch.zeros((shots, info.words_m[0]), dtype=torch.int32, device="cuda")
+    code.sample(L.NOISE_X, p, shots, 7, 0, err_x=err, syn_z=syn_d)
+    o = L.opts(side=0, p=p)
+    corr, st, it, post = _iterated(L, code, o, 2, syn_d, shots)
+    c0 = _decode(L, code, o, syn_d, shots)
+    redo = np.nonzero((c0[1] & L.ST_CONVERGED) == 0)[0]
+    assert 0.2 < redo.size / shots < 0.7
+    rows = np.unique(np.concatenate([[0, 1, 1023, 1024, shots - 1], redo[:2], redo[[redo.size // 2]],
+                                     redo[np.searchsorted(redo, 1 << 17):][:2], redo[-2:]]))
+    alone = _iterated(L, code, o, 2, syn_d[torch.from_numpy(rows).cuda()].contiguous(), rows.size)
+    assert _same(alone, (corr[rows], st[rows], it[rows], post[rows]))
+    keep = np.setdiff1d(np.arange(shots), redo)[:1000]
+    assert _same((corr[keep], st[keep], it[keep], post[keep]), tuple(a[keep] for a in c0))
+    two = redo[[0, redo.size - 1]]
+    syn2 = philox.unpack_bits(syn_d[torch.from_numpy(two).cuda()].cpu().numpy().view(np.uint32), info.m[0])
+    prior = _prior_of(c0[3][two])
+    lam, _ = _merged_llr(L, code, o, _syn_dev(code, 0, syn2), 2, prior)
+    wc, wst, wit, wpost = olead.min_sum(oc.sides[0].H, oc.sides[0].m_l, syn2, lam, 32)
+    assert (philox.unpack_bits(corr[two].view(np.uint32), oc.n) == wc).all()
+    assert (st[two] == wst).all() and (it[two] == c0[2][two] + wit).all()
+    assert (post[two].view(np.uint32) == wpost.view(np.uint32)).all()
+
+
+def test_edges(codes, L):
+    inst, code, oc = codes["PSL(2,7)"]
+    info = code.info
+    o = L.opts(side=0, p=0.03)
+    ws = torch.empty(code.iterated_workspace_bytes(o, 8), dtype=torch.uint8, device="cuda")
+    # empty batch: nothing read or written
+    code.decode_iterated(o, 3, None, 0, None, None, workspace=ws)
+    # zero syndromes: every shot converges at iteration 0, no further round runs
+    zs = torch.zeros((8, info.words_m[0]), dtype=torch.int32, device="cuda")
+    corr, st, it, post = _iterated(L, code, o, 3, zs, 8)
+    assert not corr.any() and (st == L.ST_CONVERGED).all() and (it == 0).all()
+    _, syn = _errors(oc, 0, 0.03, 8, seed=4)
+    syn_d = _syn_dev(code, 0, syn)
+    c, s, i, pst = _out(code, 8)
+    bad = [dict(rounds=0), dict(rounds=65), dict(llr=None), dict(ws=ws[:1024]), dict(ws=ws[16:])]
+    for b in bad:
+        with pytest.raises(L.LeadError):
+            code.decode_iterated(o, b.get("rounds", 2), syn_d, 8, c, s, i, b.get("llr", pst),
+                                 b.get("ws", ws))
+    # a local code the per-qubit path cannot serve is refused before round 0 writes anything
+    # (every standard code is served, so only the options can be wrong here: alpha out of range)
+    with pytest.raises(L.LeadError):
+        code.decode_iterated(L.opts(side=0, p=0.03, alpha=1.5), 2, syn_d, 8, c, s, i, pst, ws)
+    torch.cuda.synchronize()
+    assert (s == 0).all() and (i == -1).all()
