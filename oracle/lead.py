@@ -292,11 +292,11 @@ def redecode(code: TannerCode, side_id: int, syn: np.ndarray, post: np.ndarray, 
              max_iter: int = 32, use_lead: bool = True, precision: int = PREC_FP32):
     """One round of iterated LEAD (an extension; the paper runs Algorithm 1 once): the per-qubit
     prior is the flip probability the last global posterior LLR states, p_i = 1 / (1 + e^{post_i})
-    (``local.sigmoid_f32``), clamped to [2^-23, 1 - 2^-23]; then Algorithm 1 with that prior:
+    (``local.flip_prob_f32``, binary32), clamped to [2^-23, 1 - 2^-23]; then Algorithm 1 with that prior:
     Phase 1 the exact local posterior under the product prior with its least-cost decision and
     boost (``local_priors``), Phase 2 ``merge_priors_f32``, Phase 3 ``min_sum``. use_lead=False
     hands lambda(p_i) to min-sum directly. Returns (corr, status, iters, post) as ``decode``."""
-    prior = np.clip(local.sigmoid_f32(post), local.P_MIN_F, local.P_MAX_F).astype(np.float32)
+    prior = np.clip(local.flip_prob_f32(post), local.P_MIN_F, local.P_MAX_F).astype(np.float32)
     if use_lead:
         q, _ = local_priors(code, side_id, syn, prior)
         lam = merge_priors_f32(code, side_id, q, alpha)

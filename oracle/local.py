@@ -354,6 +354,33 @@ def sigmoid_f32(post: np.ndarray) -> np.ndarray:
     return (1.0 / (1.0 + exp_series_f64(x))).astype(np.float32)
 
 
+# Binary32 constants of flip_prob_f32: 1/ln 2 and ln 2 = LN2_HI_F + LN2_LO_F with LN2_HI_F =
+# 0.693359375 (9 significant bits, so k * LN2_HI_F is exact for |k| <= 25), each the binary64
+# value rounded once to binary32; the Taylor coefficients 1/n! likewise.
+INV_LN2_F = np.float32(1.4426950408889634)
+LN2_HI_F = np.float32(0.693359375)
+LN2_LO_F = np.float32(0.6931471805599453 - 0.693359375)
+INV_FACT_F = [np.float32(1.0 / float(factorial(n))) for n in range(8)]
+FLIP_CLAMP = np.float32(17.0)
+
+
+def flip_prob_f32(post: np.ndarray) -> np.ndarray:
+    """p = 1 / (1 + e^post), the flip probability a posterior LLR states, in binary32 arithmetic
+    with every operation rounded to nearest: post clamped to [-17, 17] (beyond it p lies outside
+    [2^-23, 1 - 2^-23], where the per-qubit prior is clamped anyway); k = rint(post / ln 2);
+    r = (post - k LN2_HI_F) - k LN2_LO_F; e^r by its Taylor series through r^7 in Horner form;
+    e^post = e^r 2^k (exact); then the add and the divide."""
+    x = np.clip(np.asarray(post, dtype=np.float32), -FLIP_CLAMP, FLIP_CLAMP).astype(np.float32)
+    k = np.rint((x * INV_LN2_F).astype(np.float32)).astype(np.float32)
+    r = ((x - (k * LN2_HI_F).astype(np.float32)).astype(np.float32) - (k * LN2_LO_F).astype(np.float32))
+    r = r.astype(np.float32)
+    s = np.full(x.shape, INV_FACT_F[7], dtype=np.float32)
+    for n in range(6, -1, -1):
+        s = ((s * r).astype(np.float32) + INV_FACT_F[n]).astype(np.float32)
+    e = np.ldexp(s, k.astype(np.int32)).astype(np.float32)
+    return (np.float32(1.0) / (np.float32(1.0) + e).astype(np.float32)).astype(np.float32)
+
+
 def llr_tables():
     """(T0, T1) binary32 node values and slopes of lambda(p) = ln((1 - p)/p) on [2^-23, 1/2]."""
     i = np.arange(LLR_NODES + 1, dtype=np.uint32)

@@ -10,7 +10,10 @@ What fixes it independently of its own code:
 * a zero posterior is the uninformative prior 1/2: every local coset of a linear code with no
   unit vector in its dual is balanced in every position, so q_j = 1/2 exactly, the merge gives
   lambda = 0, and min-sum can never leave the zero decision;
-* rounds only touch unconverged shots, converged outputs satisfy H e = s, iterations add up.
+* rounds only touch unconverged shots, converged outputs satisfy H e = s, iterations add up;
+* the binary32 conversion p = 1/(1 + e^post) stays within 3 units in the last place of the
+  closed form, is monotone, gives exactly 1/2 at 0, and lands beyond the prior clamp outside
+  [-17, 17].
 """
 import numpy as np
 import pytest
@@ -48,7 +51,7 @@ def test_signed_posterior_recovers_the_error(sl3, side_id, use_lead):
 def test_zero_posterior_is_uninformative(sl3):
     _, code = sl3
     e, syn = _shots(code, 0, 0.08, 6, seed=7)
-    half = local.sigmoid_f32(np.zeros((6, code.n), dtype=np.float32))
+    half = local.flip_prob_f32(np.zeros((6, code.n), dtype=np.float32))
     assert (half == np.float32(0.5)).all()
     q, _ = lead.local_priors(code, 0, syn, half)
     assert (q == 0.5).all()
@@ -81,3 +84,16 @@ def test_rounds_touch_only_unconverged_shots(sl3):
     c1, s1, i1, _ = lead.redecode(code, 0, syn[redo], p0[redo])
     c2, s2, i2, _ = lead.decode_iterated(code, 0, syn, 0.07, rounds=2)
     assert (c2[redo] == c1).all() and (s2[redo] == s1).all() and (i2[redo] == i0[redo] + i1).all()
+
+
+def test_flip_probability_binary32():
+    x = np.linspace(-17.0, 17.0, 400001).astype(np.float32)
+    p = local.flip_prob_f32(x)
+    exact = 1.0 / (1.0 + np.exp(x.astype(np.float64)))
+    ulp = np.spacing(exact.astype(np.float32)).astype(np.float64)
+    assert (np.abs(p.astype(np.float64) - exact) <= 3.0 * ulp).all()
+    assert (np.diff(p.astype(np.float64)) <= 0).all()
+    assert local.flip_prob_f32(np.float32(0.0)) == np.float32(0.5)
+    far = np.array([17.0, 30.0, 1e30, np.inf], dtype=np.float32)
+    assert (local.flip_prob_f32(far) < local.P_MIN_F).all()
+    assert (local.flip_prob_f32(-far) >= local.P_MAX_F).all()
