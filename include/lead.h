@@ -345,8 +345,10 @@ int lead_decode_priors(const lead_code* code, const lead_decode_opts* opts, cons
  * lead_decode_iterated -- iterated LEAD, an extension: the paper runs Algorithm 1 once. Round 0
  * is lead_decode. Each further round takes the shots whose status lacks LEAD_ST_CONVERGED,
  * turns every qubit's last global posterior LLR post_i into a per-qubit prior
- * p_i = 1 / (1 + e^{post_i}) (post clamped to [-88, 88]; the exponential in binary64 by
- * Cody-Waite reduction and its Taylor series through degree 14, one rounding to binary32), and
+ * p_i = 1 / (1 + e^{post_i}) in binary32 (post clamped to [-17, 17], beyond which p falls
+ * outside the prior clamp [2^-23, 1 - 2^-23]; e^post by Cody-Waite reduction with ln 2 split
+ * as 0.693359375 + its binary32 remainder and the Taylor series of e^r through degree 7 in
+ * Horner form, every operation rounded to nearest), and
  * decodes those shots again as lead_decode_priors does with that prior: the exact local
  * posterior under the product prior with use_lead == 1 (opts->estimator applies to round 0
  * only), the prior LLR alone with use_lead == 0. Shots that converged keep their result.

@@ -3,7 +3,7 @@
 // an extension built from its parts:
 //   round 0: lead_decode (Phases 1-3 with the channel prior);
 //   round r >= 1: for the shots without LEAD_ST_CONVERGED, p_i = 1 / (1 + e^{post_i}) from the
-//     previous round's posterior LLR (sigmoid_f32: binary64 exponential, one rounding), then
+//     previous round's posterior LLR (flip_prob_f32, binary32), then
 //     lead_decode_priors (Phase 1 as the exact local posterior under those priors, Phase 2,
 //     Phase 3) on a compacted batch, and the results scattered back.
 // Kernels here: the ordered compaction of unconverged shots, the gather (syndromes + priors) and
@@ -23,6 +23,29 @@ constexpr int kMaxRounds = 64;
 constexpr int kSelectThreads = 1024;
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// p = 1 / (1 + e^x), the flip probability of a posterior LLR x, in binary32 with every operation
+// rounded to nearest (no contraction): x clamped to [-17, 17] (beyond it p lies outside
+// [2^-23, 1 - 2^-23], where the per-qubit prior is clamped anyway); k = rint(x / ln 2);
+// r = (x - k LN2_HI) - k LN2_LO with LN2_HI = 0.693359375 (9 significant bits: k LN2_HI is exact
+// for |k| <= 25); e^r by its Taylor series through r^7 in Horner form; e^x = e^r 2^k (exact).
+// Each constant is its binary64 value rounded once to binary32.
+__device__ __forceinline__ float flip_prob_f32(float x) {
+  constexpr float kInvLn2 = (float)1.4426950408889634;
+  constexpr float kLn2Hi = 0.693359375f;
+  constexpr float kLn2Lo = (float)(0.6931471805599453 - 0.693359375);
+  constexpr float kInvFact[8] = {(float)(1.0 / 1.0),  (float)(1.0 / 1.0),   (float)(1.0 / 2.0),
+                                 (float)(1.0 / 6.0),  (float)(1.0 / 24.0),  (float)(1.0 / 120.0),
+                                 (float)(1.0 / 720.0), (float)(1.0 / 5040.0)};
+  x = fminf(fmaxf(x, -17.0f), 17.0f);
+  const float k = rintf(__fmul_rn(x, kInvLn2));
+  const float r = __fsub_rn(__fsub_rn(x, __fmul_rn(k, kLn2Hi)), __fmul_rn(k, kLn2Lo));
+  float s = kInvFact[7];
+#pragma unroll
+  for (int n = 6; n >= 0; --n) s = __fadd_rn(__fmul_rn(s, r), kInvFact[n]);
+  const float e = __fmul_rn(s, __int_as_float(((int)k + 127) << 23));
+  return __fdiv_rn(1.0f, __fadd_rn(1.0f, e));
+}
 
 // Indices of the shots whose status lacks LEAD_ST_CONVERGED, in increasing order, and their
 // number. One CTA walks the batch 1024 shots at a time: a ballot per warp, the 32 warp counts
@@ -54,7 +77,7 @@ __global__ void __launch_bounds__(kSelectThreads) select_unconverged_kernel(cons
 }
 
 // Compacted inputs of the next round: row j takes shot list[j]'s syndrome and, per qubit, the
-// prior p = sigmoid_f32(post) of that shot's last posterior LLR.
+// prior p = flip_prob_f32(post) of that shot's last posterior LLR.
 __global__ void iter_gather_kernel(const int32_t* __restrict__ list, int64_t cnt, const uint32_t* __restrict__ syn,
                                    int wm, const float* __restrict__ post, int n, uint32_t* __restrict__ syn_c,
                                    float* __restrict__ prior_c) {
@@ -66,7 +89,7 @@ __global__ void iter_gather_kernel(const int32_t* __restrict__ list, int64_t cnt
   }
   for (int64_t t = t0; t < cnt * n; t += stride) {
     const int64_t j = t / n;
-    prior_c[t] = sigmoid_f32(post[(int64_t)list[j] * n + (t - j * n)]);
+    prior_c[t] = flip_prob_f32(post[(int64_t)list[j] * n + (t - j * n)]);
   }
 }
 

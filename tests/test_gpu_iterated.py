@@ -3,7 +3,7 @@
 Bar: bit-exact wherever the arithmetic is fixed, stage by stage:
 * one round is lead_decode, bit for bit;
 * every further round equals lead_decode_priors on the unconverged shots with the prior
-  clip(sigmoid_f32(post)) that the oracle computes from the previous round's posterior: so the
+  clip(flip_prob_f32(post)) that the oracle computes from the previous round's posterior: so the
   conversion and the compaction are bit-exact, and the scatter keeps converged shots untouched;
 * that round's global min-sum equals the oracle's min_sum on the merged prior LLRs the kernel
   computes from the same priors (corrections, status, iterations, posteriors), and on SL(2,3)
@@ -96,7 +96,7 @@ def _merged_llr(L, code, o, syn_d, shots, prior):
 
 
 def _prior_of(post):
-    return np.clip(olocal.sigmoid_f32(post), olocal.P_MIN_F, olocal.P_MAX_F).astype(np.float32)
+    return np.clip(olocal.flip_prob_f32(post), olocal.P_MIN_F, olocal.P_MAX_F).astype(np.float32)
 
 
 def _same(a, b):
