@@ -384,13 +384,16 @@ int lead_decode_iterated(const lead_code* code, const lead_decode_opts* opts, in
  *    sums; ties to the earlier candidate;
  *  - corr[shot] is replaced by the chosen correction (it satisfies H e = s whenever s is in the
  *    column space of H, as for every syndrome of an error) and status[shot] gains LEAD_ST_OSD.
- *  order 0..6; codes with n <= 4096 and m[side] <= 4096.
+ *  order 0..6; codes with n and m[side] up to 65535 whose per-check elimination state (18 bytes
+ *  per check of the side plus n/4 bytes) fits in one CTA's shared memory: m up to about 12 000.
  *  syn (dev, shots x words_m[side]); prior (dev, shots x n float, nullable: the channel LLR of
  *  opts->p for every qubit; for LEAD pass lead_local_estimate's output, the prior the global
  *  decoder used); post (dev, shots x n float): lead_decode's posterior LLRs; status (dev, in/out);
  *  corr (dev, in/out, shots x words_n).
  *  workspace (dev, 16-byte aligned) >= lead_osd_workspace_bytes: one m x ceil(n/64) x 8-byte
- *  matrix per CTA slot (at most two CTAs per SM); a smaller workspace runs fewer slots.
+ *  matrix per CTA slot (at most two CTAs per SM) and, for codes whose sort and per-column arrays
+ *  exceed shared memory, those arrays (about 8 np + 8 n + 8 m bytes, np the power of two >= n)
+ *  per slot; a smaller workspace runs fewer slots.
  * Errors: LEAD_EINVAL, LEAD_ESTATE, LEAD_ECUDA.
  */
 size_t lead_osd_workspace_bytes(const lead_code* code, const lead_decode_opts* opts, int64_t shots);

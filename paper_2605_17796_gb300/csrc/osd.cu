@@ -23,8 +23,9 @@ int check_device(const lead_code* code);
 namespace {
 
 constexpr int kOsdThreads = 512;
-constexpr int kOsdMaxN = 4096;        // sort and per-column arrays in shared memory
-constexpr int kOsdMaxM = 4096;
+constexpr int kOsdMaxN = 65535;       // column and row indices are stored as uint16
+constexpr int kOsdMaxM = 65535;
+constexpr size_t kOsdMaxSmem = 227u * 1024u;
 constexpr int kOsdMaxOrder = 6;
 constexpr unsigned long long kNone = ~0ull;
 
@@ -39,6 +40,8 @@ struct OsdArgs {
   uint32_t* corr;
   const uint16_t* views;      // order x nl qubit ids
   unsigned long long* scratch;  // gridDim.x slots of m x w64 words
+  unsigned char* garr;          // gridDim.x slots of the arrays kept in global memory (big codes)
+  size_t garr_bytes;            // bytes per slot of garr
 };
 
 __device__ __forceinline__ unsigned int order_key(float x) {
@@ -88,58 +91,73 @@ __device__ void block_min_pair(long long& cost, int& idx, long long* redc, int* 
   __syncthreads();
 }
 
-// Shared-memory layout of one CTA (bytes from the start of dynamic shared memory).
+// Layout of one CTA's arrays. The elimination state of every row (panel word, pivot mask, used
+// flag, carried syndrome bit), the pivot-column bitmaps and the reduction scratch always live in
+// shared memory. The sort keys (later the staged pivot rows), the column order and weights and the
+// per-pivot arrays live there too when everything fits (`big` false); otherwise (`big` true) they
+// move to the CTA's slot of global scratch, which stays in L1/L2.
 struct OsdLayout {
   int np;                                  // sort size: the power of two >= n
-  size_t keys, ord, pos, wc, piv, rowof, dval, synb, ispiv, solq, panel, amask, used, misc, total;
+  bool big;
+  size_t keys, ord, pos, wc, piv, rowof, dval;              // shared (small) or global (big) offsets
+  size_t synb, ispiv, solq, panel, amask, used, misc;       // shared offsets
+  size_t smem, gmem;                                        // bytes of each
 };
 
-__host__ __device__ inline OsdLayout osd_layout(int n, int m) {
+__host__ __device__ inline OsdLayout osd_layout(int n, int m, bool big) {
   OsdLayout L{};
+  L.big = big;
   L.np = 1;
   while (L.np < n) L.np <<= 1;
-  size_t o = 0;
-  auto take = [&](size_t bytes) {
+  size_t so = 0, go = 0;
+  auto take = [](size_t& o, size_t bytes) {
     const size_t at = o;
     o = (o + bytes + 15) & ~size_t(15);
     return at;
   };
+  size_t& mo = big ? go : so;              // where the movable arrays go
   // the sort keys, later the 64 staged pivot rows of a panel (64 x ceil(n/64) words)
   const size_t w64 = (size_t)(n + 63) / 64;
-  L.keys = take(sizeof(unsigned long long) * (L.np > (int)(64 * w64) ? L.np : 64 * w64));
-  L.ord = take(sizeof(uint16_t) * n);
-  L.pos = take(sizeof(uint16_t) * n);
-  L.wc = take(sizeof(int) * n);
-  L.piv = take(sizeof(uint16_t) * m);          // pivot column of reduced row r
-  L.rowof = take(sizeof(uint16_t) * m);        // physical row holding reduced row r
-  L.dval = take(sizeof(int) * m);
-  L.synb = take(m);
-  L.ispiv = take(sizeof(uint32_t) * ((n + 31) / 32));
-  L.solq = take(sizeof(uint32_t) * ((n + 31) / 32));
-  L.panel = take(sizeof(unsigned long long) * m);   // the current panel word of every row
-  L.amask = take(sizeof(unsigned long long) * m);   // which of the panel's pivot rows each row took
-  L.used = take(m);                                 // row already serves as a pivot
-  L.misc = take(sizeof(long long) * 2 * (kOsdThreads / 32) + 64 + 64 * sizeof(int) + 64);
-  L.total = o;
+  L.keys = take(mo, sizeof(unsigned long long) * (L.np > (int)(64 * w64) ? L.np : 64 * w64));
+  L.ord = take(mo, sizeof(uint16_t) * n);
+  L.pos = take(mo, sizeof(uint16_t) * n);
+  L.wc = take(mo, sizeof(int) * n);
+  L.piv = take(mo, sizeof(uint16_t) * m);          // pivot column of reduced row r
+  L.rowof = take(mo, sizeof(uint16_t) * m);        // physical row holding reduced row r
+  L.dval = take(mo, sizeof(int) * m);
+  L.synb = take(so, m);
+  L.ispiv = take(so, sizeof(uint32_t) * ((n + 31) / 32));
+  L.solq = take(so, sizeof(uint32_t) * ((n + 31) / 32));
+  L.panel = take(so, sizeof(unsigned long long) * m);   // the current panel word of every row
+  L.amask = take(so, sizeof(unsigned long long) * m);   // which of the panel's pivot rows each row took
+  L.used = take(so, m);                                 // row already serves as a pivot
+  L.misc = take(so, sizeof(long long) * 2 * (kOsdThreads / 32) + 64 + 64 * sizeof(int) + 64);
+  L.smem = so;
+  L.gmem = (go + 255) / 256 * 256;
   return L;
 }
 
-__global__ void __launch_bounds__(kOsdThreads) osd_kernel(OsdArgs a, double p_ch, const float* __restrict__ t0,
+// BIG selects where the movable arrays live (see OsdLayout); a template parameter, so that in
+// the shared-memory variant the compiler sees shared-memory addresses. WIDE: rows of more than
+// 64 words, applied in 64-word chunks.
+template <bool BIG, bool WIDE>
+__global__ void __launch_bounds__(kOsdThreads, 2) osd_kernel(OsdArgs a, double p_ch, const float* __restrict__ t0,
                                                           const float* __restrict__ t1,
                                                           __grid_constant__ const SideParams P) {
   extern __shared__ __align__(16) unsigned char sm[];
-  const OsdLayout L = osd_layout(a.n, a.m);
-  unsigned long long* keys = reinterpret_cast<unsigned long long*>(sm + L.keys);
-  uint16_t* ord = reinterpret_cast<uint16_t*>(sm + L.ord);
-  uint16_t* pos = reinterpret_cast<uint16_t*>(sm + L.pos);
-  int* Wc = reinterpret_cast<int*>(sm + L.wc);
-  uint16_t* piv = reinterpret_cast<uint16_t*>(sm + L.piv);
-  uint16_t* rowof = reinterpret_cast<uint16_t*>(sm + L.rowof);
+  const OsdLayout L = osd_layout(a.n, a.m, BIG);
+  unsigned char* mv = BIG ? a.garr + (size_t)blockIdx.x * a.garr_bytes : sm;     // movable arrays
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(mv + L.keys);
+  uint16_t* ord = reinterpret_cast<uint16_t*>(mv + L.ord);
+  uint16_t* pos = reinterpret_cast<uint16_t*>(mv + L.pos);
+  int* Wc = reinterpret_cast<int*>(mv + L.wc);
+  uint16_t* piv = reinterpret_cast<uint16_t*>(mv + L.piv);
+  uint16_t* rowof = reinterpret_cast<uint16_t*>(mv + L.rowof);
   unsigned long long* panel = reinterpret_cast<unsigned long long*>(sm + L.panel);
   unsigned long long* amask = reinterpret_cast<unsigned long long*>(sm + L.amask);
   uint8_t* used = sm + L.used;
   unsigned long long* qrows = keys;            // staged pivot rows (after the sort)
-  int* dval = reinterpret_cast<int*>(sm + L.dval);
+  int* dval = reinterpret_cast<int*>(mv + L.dval);
   uint8_t* synb = sm + L.synb;
   uint32_t* ispiv = reinterpret_cast<uint32_t*>(sm + L.ispiv);
   uint32_t* solq = reinterpret_cast<uint32_t*>(sm + L.solq);
@@ -255,28 +273,51 @@ __global__ void __launch_bounds__(kOsdThreads) osd_kernel(OsdArgs a, double p_ch
         }
         for (int kk = tid; kk < k; kk += bd) synq[kk] = synb[kphys[kk]];
         __syncthreads();
-        // warp per row, the row's mask bits walked once (warp-uniform), lanes on words lane and
-        // lane + 32 (a row has at most 64 words: n <= 4096); the row's words are loaded first so
-        // the loads are in flight during the walk
-        const bool has0 = lane < W, has1 = lane + 32 < W;
-        for (int i = warp; i < m; i += nwarps) {
+        // warp per row, the row's mask bits walked once per 64-word chunk (warp-uniform), lanes
+        // on words w0 + lane and w0 + lane + 32; the row's words are loaded first so the loads are
+        // in flight during the walk
+        if (!WIDE) {
+          const bool has0 = lane < W, has1 = lane + 32 < W;
+          for (int i = warp; i < m; i += nwarps) {
+            const unsigned long long am = amask[i];
+            if (!am) continue;
+            unsigned long long* row = mat + (size_t)i * W;
+            const unsigned long long r0 = has0 ? row[lane] : 0ull;
+            const unsigned long long r1 = has1 ? row[lane + 32] : 0ull;
+            unsigned long long acc0 = 0ull, acc1 = 0ull;
+            unsigned int sacc = 0;
+            for (unsigned long long r = am; r; r &= r - 1) {
+              const int kk = __ffsll((long long)r) - 1;
+              const unsigned long long* q = qrows + kk * W;
+              if (has0) acc0 ^= q[lane];
+              if (has1) acc1 ^= q[lane + 32];
+              sacc ^= synq[kk];
+            }
+            if (has0) row[lane] = r0 ^ acc0;
+            if (has1) row[lane + 32] = r1 ^ acc1;
+            if (lane == 0) synb[i] ^= (uint8_t)sacc;
+          }
+        } else for (int i = warp; i < m; i += nwarps) {
           const unsigned long long am = amask[i];
           if (!am) continue;
           unsigned long long* row = mat + (size_t)i * W;
-          const unsigned long long r0 = has0 ? row[lane] : 0ull;
-          const unsigned long long r1 = has1 ? row[lane + 32] : 0ull;
-          unsigned long long acc0 = 0ull, acc1 = 0ull;
-          unsigned int sacc = 0;
-          for (unsigned long long r = am; r; r &= r - 1) {
-            const int kk = __ffsll((long long)r) - 1;
-            const unsigned long long* q = qrows + kk * W;
-            if (has0) acc0 ^= q[lane];
-            if (has1) acc1 ^= q[lane + 32];
-            sacc ^= synq[kk];
+          for (int w0 = 0; w0 < W; w0 += 64) {
+            const bool has0 = w0 + lane < W, has1 = w0 + lane + 32 < W;
+            const unsigned long long r0 = has0 ? row[w0 + lane] : 0ull;
+            const unsigned long long r1 = has1 ? row[w0 + lane + 32] : 0ull;
+            unsigned long long acc0 = 0ull, acc1 = 0ull;
+            unsigned int sacc = 0;
+            for (unsigned long long r = am; r; r &= r - 1) {
+              const int kk = __ffsll((long long)r) - 1;
+              const unsigned long long* q = qrows + (size_t)kk * W + w0;
+              if (has0) acc0 ^= q[lane];
+              if (has1) acc1 ^= q[lane + 32];
+              sacc ^= synq[kk];
+            }
+            if (has0) row[w0 + lane] = r0 ^ acc0;
+            if (has1) row[w0 + lane + 32] = r1 ^ acc1;
+            if (w0 == 0 && lane == 0) synb[i] ^= (uint8_t)sacc;
           }
-          if (has0) row[lane] = r0 ^ acc0;
-          if (has1) row[lane + 32] = r1 ^ acc1;
-          if (lane == 0) synb[i] ^= (uint8_t)sacc;
         }
         __syncthreads();
       }
@@ -367,9 +408,22 @@ __global__ void __launch_bounds__(kOsdThreads) osd_kernel(OsdArgs a, double p_ch
   }
 }
 
-size_t osd_slot_bytes(const lead_code* code, int side) {
+size_t osd_matrix_bytes(const lead_code* code, int side) {
   const size_t w64 = ((size_t)code->n + 63) / 64;
   return ((size_t)code->side[side].m * w64 * 8 + 255) / 256 * 256;
+}
+
+// The layout a side uses: everything in shared memory when it fits, else the movable arrays in
+// global scratch.
+OsdLayout osd_side_layout(const lead_code* code, int side) {
+  const OsdLayout small = osd_layout(code->n, code->side[side].m, false);
+  return small.smem <= kOsdMaxSmem ? small : osd_layout(code->n, code->side[side].m, true);
+}
+
+// Workspace of one CTA slot: its matrix, then (big codes) its global arrays.
+size_t osd_slot_bytes(const lead_code* code, int side) {
+  const OsdLayout L = osd_side_layout(code, side);
+  return osd_matrix_bytes(code, side) + (L.big ? L.gmem : 0);
 }
 
 int osd_slots(const lead_code* code, int64_t shots) {
@@ -395,17 +449,19 @@ int lead_osd(const lead_code* code, const lead_decode_opts* opts, int32_t order,
   if (!opts || opts->side < 0 || opts->side > 1 || order < 0 || order > kOsdMaxOrder || shots < 0)
     return LEAD_EINVAL;
   const HostSide& hs = code->side[opts->side];
-  if (code->n > kOsdMaxN || hs.m > kOsdMaxM) return LEAD_EINVAL;     // rows of <= 64 words
+  if (code->n > kOsdMaxN || hs.m > kOsdMaxM) return LEAD_EINVAL;     // uint16 column / row ids
   if (!prior && !(opts->p > 0.0 && opts->p < 0.5)) return LEAD_EINVAL;
   if (shots == 0) return LEAD_OK;
   if (!syn || !post || !status || !corr || !workspace || ((uintptr_t)workspace & 15)) return LEAD_EINVAL;
   const size_t slot = osd_slot_bytes(code, opts->side);
   const int slots = (int)std::min<int64_t>(osd_slots(code, shots), (int64_t)(ws_bytes / slot));
   if (slots < 1) return LEAD_EINVAL;
-  const OsdLayout L = osd_layout(code->n, hs.m);
-  if (L.total > 227u * 1024u) return LEAD_EINVAL;
-  if (L.total > 48u * 1024u)
-    LEAD_CUDA_TRY(cudaFuncSetAttribute(osd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  const OsdLayout L = osd_side_layout(code, opts->side);
+  if (L.smem > kOsdMaxSmem) return LEAD_EINVAL;
+  const bool wide = (code->n + 63) / 64 > 64;
+  auto* kern = L.big ? osd_kernel<true, true> : (wide ? osd_kernel<false, true> : osd_kernel<false, false>);
+  if (L.smem > 48u * 1024u)
+    LEAD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
   OsdArgs a{};
   a.n = code->n;
   a.m = hs.m;
@@ -423,8 +479,12 @@ int lead_osd(const lead_code* code, const lead_decode_opts* opts, int32_t order,
   a.status = status;
   a.corr = corr;
   a.views = code->dside[opts->side].views;
+  // slots matrices first, then the slots' global arrays (big codes)
+  const size_t mat_bytes = osd_matrix_bytes(code, opts->side);
   a.scratch = static_cast<unsigned long long*>(workspace);
-  osd_kernel<<<slots, kOsdThreads, L.total, (cudaStream_t)stream>>>(a, opts->p > 0.0 ? opts->p : 0.25, code->d_llr,
+  a.garr_bytes = L.big ? L.gmem : 0;
+  a.garr = static_cast<unsigned char*>(workspace) + (size_t)slots * mat_bytes;
+  kern<<<slots, kOsdThreads, L.smem, (cudaStream_t)stream>>>(a, opts->p > 0.0 ? opts->p : 0.25, code->d_llr,
                                                                      code->d_llr + kLlrNodes, hs.params);
   LEAD_CUDA_TRY(cudaGetLastError());
   return LEAD_OK;

@@ -27,7 +27,7 @@ def L():
 @pytest.fixture(scope="module")
 def codes(L):
     out = {}
-    for name in ("SL(2,3)", "PSL(2,7)"):
+    for name in ("SL(2,3)", "PSL(2,7)", "PSL(2,11)"):
         inst = workloads.standard(name, 0)
         out[name] = (inst, L.Code.from_instance(inst).prepare(0), tanner.from_instance(inst))
     return out
@@ -116,3 +116,30 @@ def test_pipeline_with_osd_leaves_no_decoder_failures(codes, L):
     assert plain.failures > plain.logical
     assert with_osd.failures == with_osd.logical
     assert with_osd.failures < plain.failures
+
+
+def test_osd_large_code(codes, L):
+    """PSL(2,11) (n = 11 880, m = 5 940): the sort and per-column arrays no longer fit in shared
+    memory and live in each slot's global scratch, and every row spans 186 words. Two
+    unconverged shots against the oracle (about 30 s of CPU each), all OSD outputs satisfy their
+    syndromes, and a one-slot workspace gives the same result."""
+    inst, code, oc = codes["PSL(2,11)"]
+    H = oc.sides[0].H
+    syn, e, corr0, st0, corr, st, post, prior = _run(L, code, oc, 0, 0.04, 6, 3, seed=5)
+    conv = (st0.cpu().numpy() & L.ST_CONVERGED) != 0
+    redo = np.nonzero(~conv)[0]
+    assert redo.size >= 2
+    only = np.zeros(len(conv), dtype=bool)
+    only[redo[:2]] = True
+    want, _ = oosd.osd_batch(H, syn, post, prior, 3, only=only)
+    got = philox.unpack_bits(corr.cpu().numpy().view(np.uint32), oc.n)
+    assert (got[only] == want[only]).all()
+    before = philox.unpack_bits(corr0.cpu().numpy().view(np.uint32), oc.n)
+    assert (got[conv] == before[conv]).all()
+    assert ((st.cpu().numpy()[~conv] & L.ST_OSD) != 0).all()
+    assert (philox.syndromes(H, got) == syn).all()
+    o = L.opts(side=0, p=0.04)
+    one = code.osd_workspace_bytes(o, 1)
+    assert code.osd_workspace_bytes(o, 6) == 6 * one
+    b = _run(L, code, oc, 0, 0.04, 6, 3, seed=5, slots_ws=one)
+    assert torch.equal(corr, b[4]) and torch.equal(st, b[5])
