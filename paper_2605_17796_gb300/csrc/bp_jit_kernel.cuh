@@ -15,8 +15,9 @@
 // The global table pa[j][t] holds the shared-memory address of the partner slot (the qubit's
 // other view) with bit 15 set when this view belongs to the smaller vertex. Each thread keeps
 // the compressed state of its ML local checks in registers: (min1, min2, meta), meta bits 0..25
-// = signs of the v2c messages by support position, 26..30 = position of the first minimum,
-// 31 = parity s_c + sum of signs. The message to position k is (-1)^(parity + sign_k) times
+// = signs of the v2c messages by support position, the first position in the highest of the
+// row's len bits (position k at bit len - 1 - k: each sign is shifted in from below), 26..30 =
+// position of the first minimum, 31 = parity s_c + sum of signs. The message to position k is (-1)^(parity + sign_k) times
 // (k == argmin ? min2 : min1), exactly the minimum over the other positions.
 //
 // Order of operations (identical to the oracle's binary32 decision track):
@@ -80,12 +81,12 @@ struct RowMag {
 // Shared-memory offset (bytes) of the word arrays behind the three NL x TS message arrays.
 constexpr unsigned int kMsgBytes = ((3u * LEAD_NL * LEAD_TS * (unsigned int)sizeof(msg_t)) + 15u) & ~15u;
 
-// New check-to-variable message of local row r to its k-th support position, from the row's
-// compressed state (m1, m2 magnitudes; meta = signs | argmin << 26 | parity << 31).
-__device__ __forceinline__ float c2v_msg(float m1, float m2, unsigned int meta, int k) {
-  const unsigned int flip = meta ^ (0u - (meta >> 31));   // bit k: sign of the message to k
+// New check-to-variable message of a local row of len positions to its k-th support position,
+// from the row's compressed state (m1, m2 magnitudes; meta = signs | argmin << 26 | parity << 31).
+__device__ __forceinline__ float c2v_msg(float m1, float m2, unsigned int meta, int k, int len) {
+  const unsigned int flip = meta ^ (0u - (meta >> 31));   // bit len-1-k: sign of the message to k
   const float mag = (k == (int)((meta >> 26) & 31u)) ? m2 : m1;
-  return __uint_as_float(__float_as_uint(mag) ^ (((flip >> k) & 1u) << 31));
+  return __uint_as_float(__float_as_uint(mag) ^ (((flip >> (len - 1 - k)) & 1u) << 31));
 }
 }  // namespace lead_jit
 
@@ -201,7 +202,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
           const float m1o = mag[r].m1(), m2o = mag[r].m2();
           const unsigned int mo = meta[r];
           const int amo = (int)((mo >> 26) & 31u);
-          const unsigned int flip = mo ^ (0u - (mo >> 31));   // bit k: sign of the old message to k
+          const unsigned int flip = mo ^ (0u - (mo >> 31));   // bit len-1-k: sign of the old message to k
           float n1 = __int_as_float(0x7F800000), n2 = __int_as_float(0x7F800000);
           int am = 0;
           unsigned int sg = 0;
@@ -209,11 +210,11 @@ lead_bp_jit(const lead::BPJitArgs a) {
           for (int k = 0; k < LEAD_KMAX; ++k) {
             if (k >= kLen[r]) break;      // constant after unrolling
             const float mago = (k == amo) ? m2o : m1o;
-            const float co = __uint_as_float(__float_as_uint(mago) ^ ((flip >> k) << 31));
+            const float co = __uint_as_float(__float_as_uint(mago) ^ ((flip >> (kLen[r] - 1 - k)) << 31));
             const float v2c = __fsub_rn(dec(Ps[kSupp[r][k] * TS + tid]), co);
             const float m = fabsf(v2c);
             // v2c is never -0 (every sum starts from +0 terms): its sign bit equals v2c < 0
-            sg |= (__float_as_uint(v2c) >> 31) << k;
+            sg = __funnelshift_l(__float_as_uint(v2c), sg, 1);
             const bool lt = m < n1;
             n2 = lt ? n1 : fminf(n2, m);
             n1 = lt ? m : n1;
@@ -232,7 +233,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
           for (int i = 0; i < LEAD_JMAX; ++i) {
             if (i >= kJLen[j]) break;     // constant after unrolling
             const int r = kJRow[j][i];
-            const float c = c2v_msg(mag[r].m1(), mag[r].m2(), meta[r], kJPos[j][i]);
+            const float c = c2v_msg(mag[r].m1(), mag[r].m2(), meta[r], kJPos[j][i], kLen[r]);
             u = (i == 0) ? c : __fadd_rn(u, c);
           }
           Us[j * TS + tid] = enc(u);
@@ -451,10 +452,10 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
           for (int k = 0; k < LEAD_KMAX; ++k) {
             if (k >= kLen[r]) break;
             const float mago = (k == amo) ? m2o : m1o;
-            const float co = __uint_as_float(__float_as_uint(mago) ^ ((flip >> k) << 31));
+            const float co = __uint_as_float(__float_as_uint(mago) ^ ((flip >> (kLen[r] - 1 - k)) << 31));
             const float v2c = __fsub_rn(dec(Ps[kSupp[r][k] * TS + tid]), co);
             const float m = fabsf(v2c);
-            sg |= (__float_as_uint(v2c) >> 31) << k;
+            sg = __funnelshift_l(__float_as_uint(v2c), sg, 1);
             const bool lt = m < n1;
             n2 = lt ? n1 : fminf(n2, m);
             n1 = lt ? m : n1;
@@ -493,7 +494,7 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
           for (int i = 0; i < LEAD_JMAX; ++i) {
             if (i >= kJLen[j]) break;     // constant after unrolling
             const int r = kJRow[j][i];
-            const float c = c2v_msg(mag[r].m1(), mag[r].m2(), meta[r], kJPos[j][i]);
+            const float c = c2v_msg(mag[r].m1(), mag[r].m2(), meta[r], kJPos[j][i], kLen[r]);
             u = (i == 0) ? c : __fadd_rn(u, c);
           }
           Us[j * TS + tid] = enc(u);
