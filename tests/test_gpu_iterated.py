@@ -270,3 +270,26 @@ def test_edges(codes, L):
         code.decode_iterated(L.opts(side=0, p=0.03, alpha=1.5), 2, syn_d, 8, c, s, i, pst, ws)
     torch.cuda.synchronize()
     assert (s == 0).all() and (i == -1).all()
+
+
+def test_pipeline_rounds(codes, L):
+    """The Monte-Carlo pipeline with rounds = 2 counts what lead_decode_iterated plus lead_check
+    give on the same sampled shots, and fixes shots that one round leaves unconverged."""
+    from paper_2605_17796_gb300.pipeline import Pipeline
+    inst, code, oc = codes["PSL(2,7)"]
+    info = code.info
+    shots, p = 3000, 0.03
+    pipe = Pipeline(code, 4096, 0)
+    one = pipe.run(L.NOISE_X, p, shots, seed=2)
+    two = pipe.run(L.NOISE_X, p, shots, seed=2, rounds=2)
+    assert two.failures < one.failures and two.not_converged < one.not_converged
+    err = torch.zeros((shots, info.words_n), dtype=torch.int32, device="cuda")
+    syn_d = torch.zeros((shots, info.words_m[0]), dtype=torch.int32, device="cuda")
+    code.sample(L.NOISE_X, p, shots, 2, 0, err_x=err, syn_z=syn_d)
+    corr, st, it, _ = _iterated(L, code, L.opts(side=0, p=p), 2, syn_d, shots)
+    fail = torch.zeros(shots, dtype=torch.uint8, device="cuda")
+    code.check(0, err, torch.from_numpy(corr).cuda(), shots, fail)
+    assert int((fail != 0).sum()) == two.failures
+    assert int(it.astype(np.int64).sum()) == two.iters_sum
+    with pytest.raises(ValueError):
+        pipe.run(L.NOISE_X, p, 100, seed=2, rounds=2, osd_order=3)
