@@ -59,6 +59,25 @@ __device__ __forceinline__ float dec(msg_t h) {
 #endif
 __device__ __forceinline__ float rnd(float v) { return dec(enc(v)); }
 
+// Hard decisions of a thread's NL slots as two words, each decision shifted in from below with
+// one funnel shift: slot j < 32 ends at bit min(NL, 32) - 1 - j of lo, slot j >= 32 at bit
+// NL - 1 - j of hi (kRowLo / kRowHi hold the local rows in this layout).
+struct HardBits {
+  unsigned int lo = 0u, hi = 0u;
+  __device__ __forceinline__ void push(int j, bool one) {   // j in increasing order
+    const unsigned int w = one ? 0x80000000u : 0u;
+    if (j < 32) lo = __funnelshift_l(w, lo, 1);
+    else hi = __funnelshift_l(w, hi, 1);
+  }
+  __device__ __forceinline__ bool get(int j) const {
+    constexpr int nlo = LEAD_NL < 32 ? LEAD_NL : 32;
+    return j < 32 ? (lo >> (nlo - 1 - j)) & 1u : (hi >> (LEAD_NL - 1 - j)) & 1u;
+  }
+  __device__ __forceinline__ unsigned int row_parity(int r) const {
+    return (unsigned int)(__popc(lo & kRowLo[r]) + (LEAD_NL > 32 ? __popc(hi & kRowHi[r]) : 0)) & 1u;
+  }
+};
+
 // The two stored magnitudes (min1, min2) of a local row's compressed state: two binary32
 // registers, or both 16-bit patterns packed in one register.
 struct RowMag {
@@ -150,7 +169,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
     __syncthreads();
     bool mydone = !act;
     for (int t = 0;; ++t) {
-      unsigned long long hm = 0;
+      HardBits hm;
       unsigned int bad = 0;
       if (!mydone) {
 #pragma unroll
@@ -161,10 +180,10 @@ lead_bp_jit(const lead::BPJitArgs a) {
           const float lj = dec(Ls[j * TS + tid]);
           const msg_t pe = enc((pa >> 15) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo));
           Ps[j * TS + tid] = pe;
-          hm |= (unsigned long long)(dec(pe) < 0.0f) << j;
+          hm.push(j, dec(pe) < 0.0f);
         }
 #pragma unroll
-        for (int r = 0; r < ML; ++r) bad |= (unsigned int)(__popcll(hm & kRowMask[r]) ^ (sv >> r)) & 1u;
+        for (int r = 0; r < ML; ++r) bad |= (hm.row_parity(r) ^ (sv >> r)) & 1u;
       }
       bool conv;
       if (LEAD_SPB == 1) {
@@ -181,7 +200,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
         for (int j = 0; j < NL; ++j) {
           if (__ldg(PA + j * TS + tid) >> 15) {
             const int q = __ldg(a.views + v * NL + j);
-            if ((hm >> j) & 1) atomicOr(cb + sl * a.words_n + (q >> 5), 1u << (q & 31));
+            if (hm.get(j)) atomicOr(cb + sl * a.words_n + (q >> 5), 1u << (q & 31));
             if (a.llr) a.llr[shot * a.n + q] = dec(Ps[j * TS + tid]);
           }
         }
@@ -393,7 +412,7 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
     }
     cluster_sync();             // zeroed U and cleared flags visible to the whole cluster
     for (int t = 0;; ++t) {
-      unsigned long long hm = 0;
+      HardBits hm;
       unsigned int bad = 0;
       if (lane_ok) {
         // partner sums in groups of kPartnerGroup slots: all reads of a group are issued before
@@ -426,12 +445,12 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
               const msg_t pe =
                   enc(((first >> g) & 1u) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo));
               Ps[j * TS + tid] = pe;
-              hm |= (unsigned long long)(dec(pe) < 0.0f) << j;
+              hm.push(j, dec(pe) < 0.0f);
             }
           }
         }
 #pragma unroll
-        for (int r = 0; r < ML; ++r) bad |= (unsigned int)(__popcll(hm & kRowMask[r]) ^ (sv >> r)) & 1u;
+        for (int r = 0; r < ML; ++r) bad |= (hm.row_parity(r) ^ (sv >> r)) & 1u;
         if (bad) red_cluster_or(flag0 + 4u * (t & 1), 1u);
       }
       if (rank == 0 && tid == 0) flags[(t + 1) & 1] = 0u;
@@ -473,7 +492,7 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
           for (int j = 0; j < NL; ++j) {
             if (cluster_partner(a.pa, j, v, V).first) {
               const int q = __ldg(a.views + v * NL + j);
-              if ((hm >> j) & 1) atomicOr(cb + (q >> 5), 1u << (q & 31));
+              if (hm.get(j)) atomicOr(cb + (q >> 5), 1u << (q & 31));
               if (a.llr) a.llr[g0 * a.n + q] = dec(Ps[j * TS + tid]);
             }
           }

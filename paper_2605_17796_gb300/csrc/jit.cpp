@@ -108,6 +108,21 @@ std::string prelude(const lead_code* code, int side, const Geometry& g, int prec
   }
   s << "};\n__device__ constexpr unsigned long long kRowMask[" << P.m_l << "] = {";
   for (int r = 0; r < P.m_l; ++r) s << (r ? "," : "") << P.rowmask[r] << "ull";
+  // the same rows over the two words of the kernel's hard-decision bits: local index j < 32 at
+  // bit nlo - 1 - j of the low word (nlo = min(nl, 32)), j >= 32 at bit nl - 1 - j of the high one
+  const int nlo = std::min(code->nl, 32);
+  for (int part = 0; part < 2; ++part) {
+    s << "};\n__device__ constexpr unsigned int " << (part ? "kRowHi" : "kRowLo") << "[" << P.m_l << "] = {";
+    for (int r = 0; r < P.m_l; ++r) {
+      unsigned int w = 0;
+      for (int j = 0; j < code->nl; ++j) {
+        if (!((P.rowmask[r] >> j) & 1ull)) continue;
+        if (part == 0 && j < 32) w |= 1u << (nlo - 1 - j);
+        if (part == 1 && j >= 32) w |= 1u << (code->nl - 1 - j);
+      }
+      s << (r ? "," : "") << w << "u";
+    }
+  }
   s << "};\n}\n";
   return s.str();
 }
