@@ -5,7 +5,8 @@
 
 For every (alpha, p) it decodes the same seeded shots with LEAD and prints one JSON line: the
 logical error rate with its Wilson 95 % interval, the fraction of shots whose min-sum did not
-converge, and the mean global iterations. One line per p is added for the standalone min-sum
+converge, the mean global iterations, and the code's parameters (n, k, Delta, A, B, the
+generator of C_A and the seeded search that chose them). One line per p is added for the standalone min-sum
 baseline (alpha = null) on the same shots. Sec. IV-C's experiment is alpha = 1 against
 alpha = 0.01 across the noise range. --estimator minsum uses local min-sum BP as the Phase-1
 local decoder instead of the exact posterior; --osd ORDER adds OSD-CS of that order after
@@ -94,7 +95,10 @@ def main(argv=None):
     ap.add_argument("--rounds", type=int, default=1)
     ap.add_argument("--chunk", type=int, default=1 << 16)
     args = ap.parse_args(argv)
-    code = lead.Code.from_instance(workloads.standard(args.code, 0)).prepare(0)
+    inst = workloads.standard(args.code, 0)
+    code = lead.Code.from_instance(inst).prepare(0)
+    params = {"n": code.info.n, "k": code.info.k, "delta": inst.delta, "A": list(inst.A), "B": list(inst.B),
+              "C_A": inst.GA.astype(int).tolist(), "search_seed": inst.seed, "search_index": inst.index}
     noise = lead.NOISE_X if args.noise == "x" else lead.NOISE_DEPOL
     ps = [float(x) for x in args.p.split(",")]
     alphas = [float(x) for x in args.alpha.split(",")]
@@ -102,6 +106,7 @@ def main(argv=None):
     for row in sweep(code, ps, alphas, args.shots, noise, args.precision, chunk=args.chunk,
                      baseline=not args.no_baseline, estimator=est, osd_order=args.osd, rounds=args.rounds):
         row["code"] = args.code
+        row["code_params"] = params
         row["noise"] = args.noise
         print(json.dumps(row), flush=True)
 
