@@ -49,6 +49,7 @@ extern "C" {
 #define LEAD_ETIMEOUT  -7   /* a bounded device wait expired                                   */
 #define LEAD_ESTATE    -8   /* code not prepared on a device, or prepared on another device    */
 #define LEAD_ENOTGROUP -9   /* the table is not a group table (identity or inverses missing)   */
+#define LEAD_ECHECK   -10   /* checked build only: a kernel index failed its bounds check      */
 
 /* noise models of lead_sample (Sec. IV-A uses depolarizing noise) */
 #define LEAD_NOISE_X      0  /* i.i.d. X flips with probability p (code capacity)              */
@@ -462,6 +463,22 @@ void lead_server_destroy(lead_server* s);
 
 /* Human-readable name of a status code (static string). */
 const char* lead_status_string(int status);
+
+/*
+ * Checked build. The library built with LEAD_CHECKED (liblead_checked.so; the binding loads it
+ * when LEAD_CHECKED=1 is set in the environment) has its kernels test every table-driven index
+ * (partner slots, vertex and qubit ids, class ids, column positions) against its bound before
+ * using it. A failed test skips the access and records the first failure on the device: site,
+ * index and bound. lead_decode, lead_decode_noalloc, lead_local_estimate,
+ * lead_local_estimate_priors, lead_decode_priors, lead_osd and lead_decode_iterated then wait
+ * for their stream and return LEAD_ECHECK. The release build compiles the tests out and never
+ * waits. This replaces a memory checker, which this build does not use.
+ */
+#define LEAD_BUILD_CHECKED 1
+/* LEAD_BUILD_* flags of the loaded library. */
+int lead_build_flags(void);
+/* The last failed check of a code, as {failures, site, index, bound}; all zero if none. */
+int lead_code_check_record(const lead_code* code, uint64_t record[4]);
 
 #ifdef __cplusplus
 }

@@ -26,6 +26,7 @@ struct BPJitArgs {
   const unsigned short* views;  // [v][j] qubit index
   const float* llr_t0;          // prior-LLR interpolation table: node values
   const float* llr_t1;          //   and slopes
+  unsigned long long* check;    // checked build: bounds-failure record {failures, site, index, bound}
 };
 
 }  // namespace lead

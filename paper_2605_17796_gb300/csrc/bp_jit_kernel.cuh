@@ -152,11 +152,13 @@ lead_bp_jit(const lead::BPJitArgs a) {
       for (int j = 0; j < NL; ++j) {
         float lj;
         if (a.lam) {
-          lj = __ldg(a.lam + (g0 + sl) * a.n + __ldg(a.views + v * NL + j));
+          const int q = __ldg(a.views + v * NL + j);
+          lj = lead::in_bounds(a.check, q, a.n, 3) ? __ldg(a.lam + (g0 + sl) * a.n + q) : 0.0f;
         } else if (a.use_lead) {
           const unsigned int addr = __ldg(PA + j * TS + tid) & 0x7FFFu;
           const unsigned int jp = addr / TS, vp = addr - jp * TS - sl * V;
-          const unsigned int svp = lead::bit_field(srow, vp * ML, ML);
+          const bool ok = lead::in_bounds(a.check, addr, NL * TS, 1) && lead::in_bounds(a.check, vp, V, 2);
+          const unsigned int svp = ok ? lead::bit_field(srow, vp * ML, ML) : 0u;
           lj = lead::merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp), a.alpha, a.llr_t0,
                                 a.llr_t1);
         } else {
@@ -175,7 +177,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
 #pragma unroll
         for (int j = 0; j < NL; ++j) {
           const unsigned int pa = __ldg(PA + j * TS + tid);
-          const float up = dec(Us[pa & 0x7FFFu]);
+          const float up = lead::in_bounds(a.check, pa & 0x7FFFu, NL * TS, 1) ? dec(Us[pa & 0x7FFFu]) : 0.0f;
           const float uo = dec(Us[j * TS + tid]);
           const float lj = dec(Ls[j * TS + tid]);
           const msg_t pe = enc((pa >> 15) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo));
@@ -200,6 +202,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
         for (int j = 0; j < NL; ++j) {
           if (__ldg(PA + j * TS + tid) >> 15) {
             const int q = __ldg(a.views + v * NL + j);
+            if (!lead::in_bounds(a.check, q, a.n, 3)) continue;
             if (hm.get(j)) atomicOr(cb + sl * a.words_n + (q >> 5), 1u << (q & 31));
             if (a.llr) a.llr[shot * a.n + q] = dec(Ps[j * TS + tid]);
           }
@@ -395,12 +398,15 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
       for (int j = 0; j < NL; ++j) {
         float lj;
         if (a.lam) {
-          lj = __ldg(a.lam + g0 * a.n + __ldg(a.views + v * NL + j));
+          const int q = __ldg(a.views + v * NL + j);
+          lj = lead::in_bounds(a.check, q, a.n, 3) ? __ldg(a.lam + g0 * a.n + q) : 0.0f;
         } else if (a.use_lead) {
           const Partner pt = cluster_partner(a.pa, j, v, V);
           const unsigned int addr = pt.addr, pr = pt.rank;
           const unsigned int jp = addr / TS, vp = pr * TS + (addr - jp * TS);
-          const unsigned int svp = lead::bit_field(syn_s, vp * ML, ML);
+          const bool ok = lead::in_bounds(a.check, addr, NL * TS, 1) && lead::in_bounds(a.check, pr, C, 4) &&
+                          lead::in_bounds(a.check, vp, V, 2);
+          const unsigned int svp = ok ? lead::bit_field(syn_s, vp * ML, ML) : 0u;
           lj = lead::merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp), a.alpha, a.llr_t0,
                                 a.llr_t1);
         } else {
@@ -431,7 +437,9 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
               const msg_t* ub = ubase[0];
 #pragma unroll
               for (int r = 1; r < C; ++r) ub = (pr == (unsigned int)r) ? ubase[r] : ub;
-              upr[g] = ub[addr];    // ordered after the previous cluster barrier (memory clobber)
+              // ordered after the previous cluster barrier (memory clobber)
+              upr[g] = (lead::in_bounds(a.check, addr, NL * TS, 1) && lead::in_bounds(a.check, pr, C, 4)) ? ub[addr]
+                                                                                                       : enc(0.0f);
               first |= (unsigned int)pt.first << g;
             }
           }
@@ -492,6 +500,7 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
           for (int j = 0; j < NL; ++j) {
             if (cluster_partner(a.pa, j, v, V).first) {
               const int q = __ldg(a.views + v * NL + j);
+              if (!lead::in_bounds(a.check, q, a.n, 3)) continue;
               if (hm.get(j)) atomicOr(cb + (q >> 5), 1u << (q & 31));
               if (a.llr) a.llr[g0 * a.n + q] = dec(Ps[j * TS + tid]);
             }

@@ -471,6 +471,7 @@ const char* lead_status_string(int status) {
     case LEAD_ETIMEOUT: return "bounded device wait expired";
     case LEAD_ESTATE: return "code not prepared on this device";
     case LEAD_ENOTGROUP: return "table is not a group table";
+    case LEAD_ECHECK: return "checked build: a kernel index failed its bounds check";
     default: return "unknown status";
   }
 }

@@ -200,6 +200,7 @@ int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* 
   a.views = code->dside[o->side].views;
   a.llr_t0 = code->d_llr;
   a.llr_t1 = code->d_llr + kLlrNodes;
+  a.check = code->d_check;
   if (!a.pa) return LEAD_EINVAL;
   return jit_launch_bp(code, o->side, o->precision, a, sm_count(code->device), stream);
 }
@@ -232,6 +233,7 @@ int lead_local_estimate(const lead_code* code, const lead_decode_opts* opts, con
   rc = launch_table(code, opts->side, opts->p, table, s, opts->estimator, nullptr);
   if (rc != LEAD_OK) return rc;
   rc = launch_local_pair(code, opts, syn, shots, llr, table, static_cast<char*>(workspace) + tb, s);
+  if (rc == LEAD_OK) return check_result(code, stream);
   if (rc != LEAD_EINVAL) return rc;
   // codes the packed view coordinates cannot describe: the direct evaluation per qubit
   auto go = [&](auto prec) -> int {
@@ -239,9 +241,10 @@ int lead_local_estimate(const lead_code* code, const lead_decode_opts* opts, con
     if (code->nl == 16) return launch_local<16, PR>(code, opts, syn, shots, llr, table, s);
     return launch_local<36, PR>(code, opts, syn, shots, llr, table, s);
   };
-  if (opts->precision == LEAD_PREC_BF16) return go(std::integral_constant<int, LEAD_PREC_BF16>{});
-  if (opts->precision == LEAD_PREC_FP16) return go(std::integral_constant<int, LEAD_PREC_FP16>{});
-  return go(std::integral_constant<int, LEAD_PREC_FP32>{});
+  if (opts->precision == LEAD_PREC_BF16) rc = go(std::integral_constant<int, LEAD_PREC_BF16>{});
+  else if (opts->precision == LEAD_PREC_FP16) rc = go(std::integral_constant<int, LEAD_PREC_FP16>{});
+  else rc = go(std::integral_constant<int, LEAD_PREC_FP32>{});
+  return rc == LEAD_OK ? check_result(code, stream) : rc;
 }
 
 int lead_decode(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn,
@@ -264,7 +267,8 @@ int lead_decode(const lead_code* code, const lead_decode_opts* opts, const uint3
     rc = launch_table(code, opts->side, opts->p, table, s, opts->estimator, nullptr);
     if (rc != LEAD_OK) return rc;
   }
-  return launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s, nullptr);
+  rc = launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s, nullptr);
+  return rc == LEAD_OK ? check_result(code, stream) : rc;
 }
 
 }  // extern "C"
@@ -329,5 +333,6 @@ extern "C" int lead_decode_noalloc(const lead_code* code, const lead_decode_opts
     rc = launch_table(code, opts->side, opts->p, table, s, opts->estimator, nullptr);
     if (rc != LEAD_OK) return rc;
   }
-  return launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s, nullptr);
+  rc = launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s, nullptr);
+  return rc == LEAD_OK ? check_result(code, stream) : rc;
 }

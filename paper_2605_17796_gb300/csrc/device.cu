@@ -344,9 +344,14 @@ int prepare_device(lead_code* code, int device) {
       return rc;
     }
   }
-  if (cudaMalloc(&code->d_llr, 2 * kLlrNodes * sizeof(float)) != cudaSuccess) {
+  if (cudaMalloc(&code->d_llr, 2 * kLlrNodes * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&code->d_check, 4 * sizeof(unsigned long long)) != cudaSuccess) {
     release_device(code);
     return LEAD_EOOM;
+  }
+  if (cudaMemset(code->d_check, 0, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+    release_device(code);
+    return LEAD_ECUDA;
   }
   llr_table_kernel<<<(kLlrNodes + 255) / 256, 256>>>(code->d_llr, code->d_llr + kLlrNodes);
   if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
@@ -382,6 +387,8 @@ void release_device(lead_code* code) {
     ds = DeviceSide{};
   }
   cudaFree(code->d_llr);
+  cudaFree(code->d_check);
+  code->d_check = nullptr;
   code->d_llr = nullptr;
   if (prev >= 0) cudaSetDevice(prev);
   code->device = -1;
@@ -418,9 +425,33 @@ int launch_table(const lead_code* code, int side, double p, float* table, cudaSt
   return LEAD_OK;
 }
 
+int check_result(const lead_code* code, void* stream) {
+#if LEAD_CHECKED
+  unsigned long long rec[4];
+  LEAD_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  LEAD_CUDA_TRY(cudaMemcpy(rec, code->d_check, sizeof(rec), cudaMemcpyDeviceToHost));
+  if (rec[0] == 0) return LEAD_OK;
+  std::memcpy(code->last_check, rec, sizeof(rec));
+  LEAD_CUDA_TRY(cudaMemset(code->d_check, 0, sizeof(rec)));
+  return LEAD_ECHECK;
+#else
+  (void)code;
+  (void)stream;
+  return LEAD_OK;
+#endif
+}
+
 }  // namespace lead
 
 extern "C" {
+
+int lead_build_flags(void) { return LEAD_CHECKED ? LEAD_BUILD_CHECKED : 0; }
+
+int lead_code_check_record(const lead_code* code, uint64_t record[4]) {
+  if (!code || !record) return LEAD_EINVAL;
+  for (int i = 0; i < 4; ++i) record[i] = code->last_check[i];
+  return LEAD_OK;
+}
 
 int lead_code_prepare(lead_code* code, int32_t device) {
   if (!code || device < 0) return LEAD_EINVAL;

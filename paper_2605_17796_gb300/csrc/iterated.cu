@@ -209,7 +209,7 @@ int lead_decode_iterated(const lead_code* code, const lead_decode_opts* opts, in
                                                                            n, corr, status, iters, llr);
     LEAD_CUDA_TRY(cudaGetLastError());
   }
-  return LEAD_OK;
+  return check_result(code, stream);
 }
 
 }  // extern "C"

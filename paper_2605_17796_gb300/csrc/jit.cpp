@@ -67,6 +67,9 @@ std::string prelude(const lead_code* code, int side, const Geometry& g, int prec
   int kmax = 1;
   for (int r = 0; r < P.m_l; ++r) kmax = std::max(kmax, P.supp_len[r]);
   std::ostringstream s;
+#if defined(LEAD_CHECKED) && LEAD_CHECKED
+  s << "#define LEAD_CHECKED 1\n";       // the checked build's kernels test their table indices
+#endif
   s << "#define LEAD_NL " << code->nl << "\n"
     << "#define LEAD_ML " << P.m_l << "\n"
     << "#define LEAD_TS " << g.ts << "\n"

@@ -82,6 +82,8 @@ struct lead_code {
   int32_t device = -1;
   lead::DeviceSide dside[2];
   float* d_llr = nullptr;            // prior-LLR interpolation table: node values, then slopes
+  unsigned long long* d_check = nullptr;   // checked build: {failures, site, index, bound}
+  mutable unsigned long long last_check[4] = {};   // the last record a call returned LEAD_ECHECK for
   std::mutex jit_mu;                 // guards the lazily compiled kernels of the 16-bit modes
 };
 
@@ -91,6 +93,9 @@ int prepare_device(lead_code* code, int device);
 void release_device(lead_code* code);
 int bp_shots_per_block(const lead_code* code);   // shots per CTA of the min-sum kernel
 size_t decode_workspace_bytes(const lead_code* code, int side);   // what lead_decode reads
+// Checked build: wait for the stream and turn a recorded bounds failure into LEAD_ECHECK (the
+// record moves to code->last_check). Release build: LEAD_OK at once.
+int check_result(const lead_code* code, void* stream);
 int priors_check(const lead_code* code, const lead_decode_opts* o);   // lead_decode_priors' argument checks
 struct BPJitArgs;
 struct Geometry {               // launch geometry of the min-sum kernel for one side

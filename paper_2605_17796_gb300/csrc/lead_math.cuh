@@ -2,7 +2,32 @@
 // library specialises at run time (NVRTC). Self-contained: no includes, so NVRTC can compile it.
 #pragma once
 
+#ifndef LEAD_CHECKED
+#define LEAD_CHECKED 0
+#endif
+
 namespace lead {
+
+// Bounds test of a table-driven index (checked builds): true when 0 <= i < n; otherwise the
+// first failure is recorded in rec = {failures, site, index, bound} and the caller skips the
+// access. Release builds compile it to `true`.
+__device__ __forceinline__ bool in_bounds(unsigned long long* rec, long long i, long long n, unsigned int site) {
+#if LEAD_CHECKED
+  if (i >= 0 && i < n) return true;
+  if (rec && atomicAdd(rec, 1ull) == 0ull) {
+    rec[1] = site;
+    rec[2] = (unsigned long long)i;
+    rec[3] = (unsigned long long)n;
+  }
+  return false;
+#else
+  (void)rec;
+  (void)i;
+  (void)n;
+  (void)site;
+  return true;
+#endif
+}
 
 // m_l-bit field starting at bit `pos` of a packed bit row (the local syndrome s_v).
 __device__ __forceinline__ unsigned int bit_field(const unsigned int* row, int pos, int len) {

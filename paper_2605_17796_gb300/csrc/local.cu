@@ -130,6 +130,7 @@ struct PairArgs {
   const float* llr_t1;
   const uint32_t* qslots;
   void* llr;                    // float, or the 16-bit pattern of the storage format
+  unsigned long long* check;    // checked build: bounds-failure record
 };
 
 // Staged local syndromes are vertex-major: sv_s[v * kSvStride + shot]; the padded row of 36
@@ -148,6 +149,8 @@ __device__ __forceinline__ void batch_llrs(const PairArgs& a, const uint16_t* sv
                                            const OutT* pair_s, int K, int64_t b0, int nsh, OutT* out) {
   for (int i = threadIdx.x; i < a.n; i += kPairThreads) {
     const uint32_t s0 = __ldg(a.qslots + 2 * i), s1 = __ldg(a.qslots + 2 * i + 1);
+    if (!in_bounds(a.check, s0, (long long)a.order * NL, 10) || !in_bounds(a.check, s1, (long long)a.order * NL, 10))
+      continue;
     const uint16_t* p0 = sv_s + (s0 / NL) * kSvStride;
     const uint16_t* p1 = sv_s + (s1 / NL) * kSvStride;
     const int j0 = (int)(s0 % NL), j1 = (int)(s1 % NL);
@@ -164,7 +167,8 @@ __device__ __forceinline__ void batch_llrs(const PairArgs& a, const uint16_t* sv
           const int e1 = (int)a1[u] * NL + j1;
           OutT v;
           if constexpr (FAST) {
-            v = pair_s[cls_s[e0] * K + cls_s[e1]];
+            const int c0 = cls_s[e0], c1 = cls_s[e1];
+            v = (in_bounds(a.check, c0, K, 11) && in_bounds(a.check, c1, K, 11)) ? pair_s[c0 * K + c1] : OutT(0);
           } else {
             const float x = merged_llr(__ldg(a.table + e0), __ldg(a.table + e1), a.alpha, a.llr_t0, a.llr_t1);
             if constexpr (PREC == LEAD_PREC_FP32) v = x;
@@ -258,6 +262,7 @@ int launch_local_pair(const lead_code* code, const lead_decode_opts* o, const ui
   a.llr_t1 = code->d_llr + kLlrNodes;
   a.qslots = code->dside[o->side].qslots;
   a.llr = llr;
+  a.check = code->d_check;
   const size_t esize = o->precision == LEAD_PREC_FP32 ? 4 : 2;
   const size_t smem = (size_t)((T + 15) & ~15) + (size_t)kPairSmem * kPairSmem * esize +
                       sizeof(uint16_t) * (size_t)kSvStride * code->order;

@@ -42,6 +42,7 @@ struct OsdArgs {
   unsigned long long* scratch;  // gridDim.x slots of m x w64 words
   unsigned char* garr;          // gridDim.x slots of the arrays kept in global memory (big codes)
   size_t garr_bytes;            // bytes per slot of garr
+  unsigned long long* check;    // checked build: bounds-failure record
 };
 
 __device__ __forceinline__ unsigned int order_key(float x) {
@@ -211,7 +212,9 @@ __global__ void __launch_bounds__(kOsdThreads, 2) osd_kernel(OsdArgs a, double p
       const int v = i / a.m_l, r = i - v * a.m_l;
       unsigned long long* row = mat + (size_t)i * W;
       for (int k = 0; k < P.supp_len[r]; ++k) {
-        const int c = pos[__ldg(a.views + v * a.nl + P.supp[r][k])];
+        const int q = __ldg(a.views + v * a.nl + P.supp[r][k]);
+        if (!in_bounds(a.check, q, n, 20)) continue;
+        const int c = pos[q];
         row[c >> 6] |= 1ull << (c & 63);
       }
       synb[i] = (uint8_t)((__ldg(a.syn + shot * a.words_m + (i >> 5)) >> (i & 31)) & 1u);
@@ -484,10 +487,11 @@ int lead_osd(const lead_code* code, const lead_decode_opts* opts, int32_t order,
   a.scratch = static_cast<unsigned long long*>(workspace);
   a.garr_bytes = L.big ? L.gmem : 0;
   a.garr = static_cast<unsigned char*>(workspace) + (size_t)slots * mat_bytes;
+  a.check = code->d_check;
   kern<<<slots, kOsdThreads, L.smem, (cudaStream_t)stream>>>(a, opts->p > 0.0 ? opts->p : 0.25, code->d_llr,
                                                                      code->d_llr + kLlrNodes, hs.params);
   LEAD_CUDA_TRY(cudaGetLastError());
-  return LEAD_OK;
+  return check_result(code, stream);
 }
 
 }  // extern "C"

@@ -394,7 +394,7 @@ int lead_local_estimate_priors(const lead_code* code, const lead_decode_opts* op
                        ml_out ? ml_out + c0 * code->order : nullptr, (cudaStream_t)stream);
     if (rc != LEAD_OK) return rc;
   }
-  return LEAD_OK;
+  return check_result(code, stream);
 }
 
 int lead_decode_priors(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn, int64_t shots,
@@ -423,7 +423,7 @@ int lead_decode_priors(const lead_code* code, const lead_decode_opts* opts, cons
                    llr ? llr + c0 * n : nullptr, nullptr, s, lam);
     if (rc != LEAD_OK) return rc;
   }
-  return LEAD_OK;
+  return check_result(code, stream);
 }
 
 }  // extern "C"

@@ -13,10 +13,15 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblead.so")
+# LEAD_CHECKED=1 selects the checked build (kernels test their table indices; failures come back
+# as LEAD_ECHECK); build it with `python -m paper_2605_17796_gb300.build --checked`.
+CHECKED = os.environ.get("LEAD_CHECKED", "0") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "liblead_checked.so" if CHECKED else "liblead.so")
 
 NOISE_X, NOISE_Z, NOISE_DEPOL = 0, 1, 2
 ST_CONVERGED, ST_MAX_ITER, ST_OSD = 1, 2, 4
+ECHECK = -10                      # checked build: a kernel index failed its bounds check
+BUILD_CHECKED = 1                 # lead_build_flags() bit of the checked build
 PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
 EST_EXACT, EST_MINSUM = 0, 1
 
@@ -106,6 +111,8 @@ EXPORTS = {
     "lead_check": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lead_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lead_build_flags": (ctypes.c_int, []),
+    "lead_code_check_record": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     "lead_server_create": (ctypes.c_int, [ctypes.POINTER(LeadServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
     "lead_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]),
@@ -119,7 +126,9 @@ EXPORTS = {
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"liblead.so is not built ({LIB_PATH}); run `python -m paper_2605_17796_gb300.build`")
+        flag = " --checked" if CHECKED else ""
+        raise ImportError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); run "
+                          f"`python -m paper_2605_17796_gb300.build{flag}`")
     lib = ctypes.CDLL(LIB_PATH)
     for name, (res, args) in EXPORTS.items():
         fn = getattr(lib, name)
@@ -331,6 +340,12 @@ class Code:
         nb = workspace.numel() * workspace.element_size() if workspace is not None else 0
         _check("lead_osd", LIB.lead_osd(self._h, ctypes.byref(opts), order, _ptr(syn), shots, _ptr(prior), _ptr(post),
                                         _ptr(status), _ptr(corr), ws, nb, _stream(stream)))
+
+    def check_record(self):
+        """The last failed bounds check of a checked build: (failures, site, index, bound)."""
+        rec = (ctypes.c_uint64 * 4)()
+        _check("lead_code_check_record", LIB.lead_code_check_record(self._h, rec))
+        return tuple(int(x) for x in rec)
 
     def check(self, side: int, err, corr, shots: int, fail, stream=None):
         _check("lead_check", LIB.lead_check(self._h, side, _ptr(err), _ptr(corr), shots, _ptr(fail),

@@ -76,6 +76,15 @@ def test_error_codes(lead):
     with pytest.raises(lead.LeadError) as e:
         lead.Code(G.mul, inst.A, inst.B, np.zeros((2, 4), dtype=np.uint8))
     assert e.value.rc == -1
+    assert b"bounds check" in lead.LIB.lead_status_string(lead.ECHECK)
+
+
+def test_release_build_is_unchecked(lead):
+    """The library the tests load by default is the release build; a code that never failed a
+    bounds check reports an all-zero record."""
+    assert not lead.CHECKED and lead.LIB.lead_build_flags() == 0
+    inst = workloads.standard("SL(2,3)", 0)
+    assert lead.Code.from_instance(inst).check_record() == (0, 0, 0, 0)
 
 
 def test_device_calls_refuse_unprepared_code(lead):
