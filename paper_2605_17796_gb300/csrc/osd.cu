@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kOsdThreads, 2) osd_kernel(OsdArgs a, double p
   uint32_t* solq = reinterpret_cast<uint32_t*>(sm + L.solq);
   long long* redc = reinterpret_cast<long long*>(sm + L.misc);
   int* redi = reinterpret_cast<int*>(redc + kOsdThreads / 32);
-  int* sh = redi + kOsdThreads / 32;          // sh[0..1] pivot search slots, sh[2..] first non-basis columns
+  int* sh = redi + kOsdThreads / 32;          // sh[0..2] pivot search slots, sh[3..] first non-basis columns
   int* kphys = sh + 16;                        // physical rows of the panel's pivots
   uint8_t* synq = reinterpret_cast<uint8_t*>(kphys + 64);
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = bd >> 5;
@@ -226,30 +226,31 @@ __global__ void __launch_bounds__(kOsdThreads, 2) osd_kernel(OsdArgs a, double p
     // row in shared memory and records, per row, which of the panel's pivot rows (as they
     // stood at the panel's start) it took; phase B applies those sums to the full rows.
     for (int i = tid; i < m; i += bd) used[i] = 0;
-    if (tid == 0) {
-      sh[0] = 0x7FFFFFFF;
-      sh[1] = 0x7FFFFFFF;
-    }
+    if (tid < 3) sh[tid] = 0x7FFFFFFF;
     __syncthreads();
-    int rank = 0;
+    // One barrier per column. Thread t owns rows t, t + bd, ...: it eliminates them and then
+    // searches them for the next column's pivot at once, so the search sees their current panel
+    // words. The pivot of the column processed as the g-th goes through slot g % 3; thread 0 frees
+    // slot (g - 1) % 3 after barrier g, when every thread has read it, well before column g + 2
+    // searches into it.
+    int rank = 0, g = 0;
     for (int pn = 0; pn < W && rank < a.rank_max; ++pn) {
       for (int i = tid; i < m; i += bd) {
         panel[i] = mat[(size_t)i * W + pn];
         amask[i] = 0ull;
       }
-      __syncthreads();
+      const int bmax = n - pn * 64 < 64 ? n - pn * 64 : 64;
+      for (int i = tid; i < m; i += bd)          // the panel's first column, own rows
+        if (!used[i] && (panel[i] & 1ull)) {
+          atomicMin(sh + g % 3, i);
+          break;
+        }
       int k = 0;
-      for (int b = 0; b < 64 && rank + k < a.rank_max; ++b) {
+      for (int b = 0; b < bmax && rank + k < a.rank_max; ++b, ++g) {
         const int col = pn * 64 + b;
-        if (col >= n) break;
-        int* slot = sh + (b & 1);
-        for (int i = tid; i < m; i += bd)
-          if (!used[i] && ((panel[i] >> b) & 1ull)) {
-            atomicMin(slot, i);
-            break;
-          }
-        __syncthreads();
-        const int pr = *slot;
+        __syncthreads();                                   // column b's slot is final
+        const int pr = sh[g % 3];
+        if (tid == 0) sh[(g + 2) % 3] = 0x7FFFFFFF;        // column b - 1's slot, read by all
         if (pr != 0x7FFFFFFF) {
           const unsigned long long pp = panel[pr], ap = amask[pr] ^ (1ull << k);
           for (int i = tid; i < m; i += bd)
@@ -257,8 +258,8 @@ __global__ void __launch_bounds__(kOsdThreads, 2) osd_kernel(OsdArgs a, double p
               panel[i] ^= pp;
               amask[i] ^= ap;
             }
+          if (pr % bd == tid) used[pr] = 1;                 // only the owner reads it
           if (tid == 0) {
-            used[pr] = 1;
             kphys[k] = pr;
             piv[rank + k] = (uint16_t)col;
             rowof[rank + k] = (uint16_t)pr;
@@ -266,9 +267,14 @@ __global__ void __launch_bounds__(kOsdThreads, 2) osd_kernel(OsdArgs a, double p
           }
           ++k;
         }
-        __syncthreads();                                   // every thread has read this slot
-        if (tid == 0) *slot = 0x7FFFFFFF;                  // free for step b + 2
+        if (b + 1 < bmax && rank + k < a.rank_max)        // the next column, own rows
+          for (int i = tid; i < m; i += bd)
+            if (!used[i] && ((panel[i] >> (b + 1)) & 1ull)) {
+              atomicMin(sh + (g + 1) % 3, i);
+              break;
+            }
       }
+      __syncthreads();                                     // pivots and panel state visible
       if (k > 0) {
         for (int idx = tid; idx < k * W; idx += bd) {
           const int kk = idx / W, w = idx - kk * W;
@@ -361,8 +367,8 @@ __global__ void __launch_bounds__(kOsdThreads, 2) osd_kernel(OsdArgs a, double p
     if (tid == 0) {
       int cnt = 0;
       for (int c = 0; c < n && cnt < a.order; ++c)
-        if (!((ispiv[c >> 5] >> (c & 31)) & 1u)) sh[2 + cnt++] = c;
-      sh[2 + kOsdMaxOrder] = cnt;
+        if (!((ispiv[c >> 5] >> (c & 31)) & 1u)) sh[3 + cnt++] = c;
+      sh[3 + kOsdMaxOrder] = cnt;
     }
     __syncthreads();
     long long wcost = cost0;
@@ -372,10 +378,10 @@ __global__ void __launch_bounds__(kOsdThreads, 2) osd_kernel(OsdArgs a, double p
       kind = 1;
       ca = bi;
     }
-    const int nt = sh[2 + kOsdMaxOrder];
+    const int nt = sh[3 + kOsdMaxOrder];
     for (int pa = 0; pa < nt; ++pa)
       for (int pb = pa + 1; pb < nt; ++pb) {
-        const int x = sh[2 + pa], y = sh[2 + pb];
+        const int x = sh[3 + pa], y = sh[3 + pb];
         long long ps = 0;
         for (int i = tid; i < rank; i += bd) {
           const unsigned long long* row = mat + (size_t)rowof[i] * W;
