@@ -102,6 +102,8 @@ struct OsdLayout {
   bool big;
   size_t keys, ord, pos, wc, piv, rowof, dval;              // shared (small) or global (big) offsets
   size_t synb, ispiv, solq, panel, amask, used, misc;       // shared offsets
+  size_t qrows;                            // big layout: the staged pivot rows in shared memory
+  bool qsm;                                //   when they fit there (else the sort keys' space)
   size_t smem, gmem;                                        // bytes of each
 };
 
@@ -133,6 +135,11 @@ __host__ __device__ inline OsdLayout osd_layout(int n, int m, bool big) {
   L.amask = take(so, sizeof(unsigned long long) * m);   // which of the panel's pivot rows each row took
   L.used = take(so, m);                                 // row already serves as a pivot
   L.misc = take(so, sizeof(long long) * 2 * (kOsdThreads / 32) + 64 + 64 * sizeof(int) + 64);
+  // big layout: the staged pivot rows get their own shared area when it fits; read by every warp
+  // for every row in phase B, they are the kernel's hottest data
+  const size_t qbytes = sizeof(unsigned long long) * 64 * w64;
+  L.qsm = big && so + qbytes <= kOsdMaxSmem;
+  if (L.qsm) L.qrows = take(so, qbytes);
   L.smem = so;
   L.gmem = (go + 255) / 256 * 256;
   return L;
@@ -157,7 +164,8 @@ __global__ void __launch_bounds__(kOsdThreads, 2) osd_kernel(OsdArgs a, double p
   unsigned long long* panel = reinterpret_cast<unsigned long long*>(sm + L.panel);
   unsigned long long* amask = reinterpret_cast<unsigned long long*>(sm + L.amask);
   uint8_t* used = sm + L.used;
-  unsigned long long* qrows = keys;            // staged pivot rows (after the sort)
+  // staged pivot rows: the sort keys' space, or their own shared area (big layout, when it fits)
+  unsigned long long* qrows = (BIG && L.qsm) ? reinterpret_cast<unsigned long long*>(sm + L.qrows) : keys;
   int* dval = reinterpret_cast<int*>(mv + L.dval);
   uint8_t* synb = sm + L.synb;
   uint32_t* ispiv = reinterpret_cast<uint32_t*>(sm + L.ispiv);
