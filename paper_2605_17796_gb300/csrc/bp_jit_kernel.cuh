@@ -64,8 +64,10 @@ __device__ __forceinline__ float rnd(float v) { return dec(enc(v)); }
 // NL - 1 - j of hi (kRowLo / kRowHi hold the local rows in this layout).
 struct HardBits {
   unsigned int lo = 0u, hi = 0u;
-  __device__ __forceinline__ void push(int j, bool one) {   // j in increasing order
-    const unsigned int w = one ? 0x80000000u : 0u;
+  // the decision [x < 0] of slot j (j in increasing order): x + 0 turns -0 into +0 and keeps
+  // every other value, so its sign bit is the decision; the shift takes that bit alone
+  __device__ __forceinline__ void push_neg(int j, float x) {
+    const unsigned int w = __float_as_uint(__fadd_rn(x, 0.0f));
     if (j < 32) lo = __funnelshift_l(w, lo, 1);
     else hi = __funnelshift_l(w, hi, 1);
   }
@@ -182,7 +184,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
           const float lj = dec(Ls[j * TS + tid]);
           const msg_t pe = enc((pa >> 15) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo));
           Ps[j * TS + tid] = pe;
-          hm.push(j, dec(pe) < 0.0f);
+          hm.push_neg(j, dec(pe));
         }
 #pragma unroll
         for (int r = 0; r < ML; ++r) bad |= (hm.row_parity(r) ^ (sv >> r)) & 1u;
@@ -453,7 +455,7 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
               const msg_t pe =
                   enc(((first >> g) & 1u) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo));
               Ps[j * TS + tid] = pe;
-              hm.push(j, dec(pe) < 0.0f);
+              hm.push_neg(j, dec(pe));
             }
           }
         }
