@@ -179,6 +179,25 @@ def test_decode_bit_exact(codes, L, name, side, p, shots, use_lead):
     assert (philox.syndromes(oc.sides[side].H, wc)[conv] == syn[conv]).all()
 
 
+@pytest.mark.parametrize("p", [0.02, 0.05, 0.08])
+def test_sl3_workload_every_shot(codes, L, p):
+    """The SL(2,3) workload in full: X noise at p = 0.02, 0.05, 0.08 with 10^4 shots each,
+    binary32 LEAD. Every shot's correction, status, iteration count, posterior and check flag
+    equals the oracle's."""
+    inst, code, oc = codes["SL(2,3)"]
+    info = code.info
+    shots = 10_000
+    e, syn = _syndromes(oc, 0, shots, p, seed=0)
+    corr, st, it, post = _decode(L, code, oc, 0, syn, p)
+    wc, wst, wit, wpost = olead.decode(oc, 0, syn, p)
+    assert (st == wst).all() and (it == wit).all()
+    assert (_bits(corr, oc.n) == wc).all()
+    assert (post.view(np.uint32) == wpost.view(np.uint32)).all()
+    fail = torch.zeros(shots, dtype=torch.uint8, device="cuda")
+    code.check(0, _dev(_words(e, info.words_n)), corr, shots, fail)
+    assert (fail.cpu().numpy() == olead.check(oc, 0, e, wc)).all()
+
+
 def test_decode_alpha_and_max_iter_edges(codes, L):
     inst, code, oc = codes["PSL(2,7)"]
     e, syn = _syndromes(oc, 0, 9, 0.02, seed=3)
