@@ -158,16 +158,7 @@ def _serving(lead, rate: float, n: int, code_psl7):
     return out
 
 
-def wilson95(k: int, n: int):
-    """Wilson score interval (95 %) of a binomial proportion k / n."""
-    if n == 0:
-        return [0.0, 1.0]
-    z = 1.959963984540054
-    ph = k / n
-    den = 1 + z * z / n
-    c = (ph + z * z / (2 * n)) / den
-    h = z / den * (ph * (1 - ph) / n + z * z / (4 * n * n)) ** 0.5
-    return [max(0.0, c - h), min(1.0, c + h)]
+from paper_2605_17796_gb300.stats import wilson95  # noqa: E402
 
 
 MODES = {"fp32": 0, "bf16": 1, "fp16": 2}

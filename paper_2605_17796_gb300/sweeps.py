@@ -27,16 +27,9 @@ import json
 
 from . import lead
 from .pipeline import Pipeline
+from .stats import wilson95  # noqa: F401  (re-exported for callers of this module)
 
 
-def wilson95(k: int, n: int):
-    """Wilson score interval (95 %) of a binomial proportion k / n."""
-    z = 1.959963984540054
-    ph = k / n
-    den = 1 + z * z / n
-    c = (ph + z * z / (2 * n)) / den
-    h = z / den * (ph * (1 - ph) / n + z * z / (4 * n * n)) ** 0.5
-    return [max(0.0, c - h), min(1.0, c + h)]
 
 
 def expected_local_iterations(code: lead.Code, side: int, p: float, estimator: int) -> float:

@@ -25,13 +25,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 
-def wilson95(k: int, n: int):
-    z = 1.959963984540054
-    ph = k / n
-    den = 1 + z * z / n
-    c = (ph + z * z / (2 * n)) / den
-    h = z / den * (ph * (1 - ph) / n + z * z / (4 * n * n)) ** 0.5
-    return [max(0.0, c - h), min(1.0, c + h)]
+from paper_2605_17796_gb300.stats import wilson95  # noqa: E402
 
 
 def main(argv=None):
