@@ -471,8 +471,9 @@ const char* lead_status_string(int status);
  * using it. A failed test skips the access and records the first failure on the device: site,
  * index and bound. lead_decode, lead_decode_noalloc, lead_local_estimate,
  * lead_local_estimate_priors, lead_decode_priors, lead_osd and lead_decode_iterated then wait
- * for their stream and return LEAD_ECHECK. The release build compiles the tests out and never
- * waits. This replaces a memory checker, which this build does not use.
+ * for their stream and return LEAD_ECHECK (a call captured into a CUDA graph does not wait; the
+ * next eager call reports what the graph's replays recorded). The release build compiles the
+ * tests out and never waits. This replaces a memory checker, which this build does not use.
  */
 #define LEAD_BUILD_CHECKED 1
 /* LEAD_BUILD_* flags of the loaded library. */

@@ -427,6 +427,11 @@ int launch_table(const lead_code* code, int side, double p, float* table, cudaSt
 
 int check_result(const lead_code* code, void* stream) {
 #if LEAD_CHECKED
+  // a call being captured into a CUDA graph cannot wait: its record is read by the next call
+  // that runs eagerly
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  LEAD_CUDA_TRY(cudaStreamIsCapturing((cudaStream_t)stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return LEAD_OK;
   unsigned long long rec[4];
   LEAD_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
   LEAD_CUDA_TRY(cudaMemcpy(rec, code->d_check, sizeof(rec), cudaMemcpyDeviceToHost));
