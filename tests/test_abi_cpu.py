@@ -115,3 +115,39 @@ def test_workspace_sizes_keep_alignment():
                 o = lead.opts(side=side, p=0.03, use_lead=use_lead)
                 assert code.workspace_bytes(o) % 256 == 0
                 assert code.priors_workspace_bytes(o, 1000) % 256 == 0
+
+
+def test_checked_build_compiles():
+    """The checked library builds, reports its flag, and its min-sum kernels (with the bounds
+    tests) specialise through NVRTC without a GPU."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-m", "paper_2605_17796_gb300.build", "--checked"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-3000:]
+    code = ("import workloads\n"
+            "from paper_2605_17796_gb300 import lead\n"
+            "assert lead.CHECKED and lead.LIB.lead_build_flags() == lead.BUILD_CHECKED\n"
+            "for name in ('SL(2,3)', 'PSL(2,7)'):\n"
+            "    lead.Code.from_instance(workloads.standard(name, 0)).compile()\n"
+            "print('ok')\n")
+    env = dict(os.environ, LEAD_CHECKED="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stderr[-3000:]
+
+
+def test_iterated_workspace_size(lead):
+    """lead_iterated_workspace_bytes: a multiple of 256 that grows by the compacted batch's
+    4 n + 4 words_m + 4 words_n + 9 bytes per shot (up to the 256-byte rounding of each region)
+    on top of the decoders' own workspace."""
+    inst = workloads.standard("PSL(2,7)", 0)
+    code = lead.Code.from_instance(inst)
+    info = code.info
+    o = lead.opts(side=0, p=0.03)
+    per_shot = 4 * info.n + 4 * info.words_m[0] + 4 * info.words_n + 9
+    for shots in (1, 1000, 1 << 16):
+        total = code.iterated_workspace_bytes(o, shots)
+        inner = max(code.workspace_bytes(o, shots), code.priors_workspace_bytes(o, shots))
+        assert total % 256 == 0
+        extra = total - inner
+        assert per_shot * shots <= extra <= per_shot * shots + 8 * 256 + 256
