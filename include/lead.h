@@ -46,7 +46,9 @@ extern "C" {
 #define LEAD_ECSS      -4   /* construction produced H_X H_Z^T != 0 (internal invariant)       */
 #define LEAD_EOOM      -5   /* host or device allocation failed                                */
 #define LEAD_ECUDA     -6   /* a CUDA runtime call failed                                      */
-#define LEAD_ETIMEOUT  -7   /* a bounded device wait expired                                   */
+#define LEAD_ETIMEOUT  -7   /* reserved for a bounded device wait that expires; no call returns
+                               it, since no kernel spins on a flag (cluster kernels use the
+                               hardware cluster barrier)                                      */
 #define LEAD_ESTATE    -8   /* code not prepared on a device, or prepared on another device    */
 #define LEAD_ENOTGROUP -9   /* the table is not a group table (identity or inverses missing)   */
 #define LEAD_ECHECK   -10   /* checked build only: a kernel index failed its bounds check      */
