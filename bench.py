@@ -102,10 +102,13 @@ def _oracle_child(shots_per_p: int, seed: int, offset: int):
 
 
 def _host_cores() -> int:
+    """Host cores this process may run on (at most 64 oracle processes: each holds its own
+    tables, a few hundred MB)."""
     try:
-        return max(1, len(os.sched_getaffinity(0)))
+        n = len(os.sched_getaffinity(0))
     except AttributeError:
-        return max(1, os.cpu_count() or 1)
+        n = os.cpu_count() or 1
+    return max(1, min(n, 64))
 
 
 def _run_oracle(shots_per_p: int, seed: int = 0, offset: int = 0, procs: int = 1):
