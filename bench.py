@@ -102,8 +102,8 @@ def _oracle_child(shots_per_p: int, seed: int, offset: int):
 
 
 def _host_cores() -> int:
-    """Host cores this process may run on (at most 64 oracle processes: each holds its own
-    tables, a few hundred MB)."""
+    """Host cores this process may run on, at most 64: each oracle process holds its own
+    tables, about 100 MB."""
     try:
         n = len(os.sched_getaffinity(0))
     except AttributeError:
