@@ -18,6 +18,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -80,7 +81,9 @@ def _instance():
 # CPU oracle (reference arm and cpu_baseline): runs in a child process, single-threaded BLAS
 # ------------------------------------------------------------------------------------------
 
-def _oracle_child(shots_per_p: int, seed: int, offset: int):
+def _oracle_child(shots_per_p: int, seed: int, offset: int, out_path: str = ""):
+    """Decodes shots offset .. offset + shots_per_p - 1 at every p of the sweep with the oracle;
+    with out_path, also saves every shot's status, iterations and packed correction there."""
     import numpy as np
     import workloads
     from oracle import lead as olead, philox, tanner
@@ -91,12 +94,19 @@ def _oracle_child(shots_per_p: int, seed: int, offset: int):
     wall0 = time.time()
     t0 = time.perf_counter()
     fails = 0
-    for p in P_SWEEP:
+    saved = {}
+    for pi, p in enumerate(P_SWEEP):
         x, _ = philox.sample_errors(philox.NOISE_X, p, seed, offset + np.arange(shots_per_p), oc.n)
         syn = philox.syndromes(oc.HZ, x)
         corr, st, it, _ = olead.decode(oc, 0, syn, p)
         fails += int((olead.check(oc, 0, x, corr) != 0).sum())
+        if out_path:
+            saved[f"corr{pi}"] = philox.pack_bits(corr, (oc.n + 31) // 32)
+            saved[f"status{pi}"] = st
+            saved[f"iters{pi}"] = it
     dt = time.perf_counter() - t0
+    if out_path:
+        np.savez(out_path, **saved)
     print(json.dumps({"shots": shots_per_p * len(P_SWEEP), "seconds": dt, "failures": fails,
                       "wall_start": wall0, "wall_end": time.time()}))
 
@@ -111,15 +121,17 @@ def _host_cores() -> int:
     return max(1, min(n, 64))
 
 
-def _run_oracle(shots_per_p: int, seed: int = 0, offset: int = 0, procs: int = 1):
+def _run_oracle(shots_per_p: int, seed: int = 0, offset: int = 0, procs: int = 1, out_dir: str = ""):
     """Runs `procs` single-threaded oracle children at once, child i on shot indices
     offset + i * shots_per_p + [0, shots_per_p) at every p. Throughput is measured over the wall
     window from the first child's start of decoding to the last child's end (table setup and
     interpreter start-up excluded); `per_core` is the mean of the children's own rates, i.e. one
-    core's rate while all of them are busy."""
+    core's rate while all of them are busy. With out_dir, child i saves its outputs as
+    out_dir/oracle_<i>.npz."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     children = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-child", str(shots_per_p),
-                                  str(seed), str(offset + i * shots_per_p)],
+                                  str(seed), str(offset + i * shots_per_p)] +
+                                 ([os.path.join(out_dir, f"oracle_{i}.npz")] if out_dir else []),
                                  stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT)
                 for i in range(procs)]
     outs = []
@@ -136,29 +148,126 @@ def _run_oracle(shots_per_p: int, seed: int = 0, offset: int = 0, procs: int = 1
 
 # ------------------------------------------------------------------------------------------
 
-def _serving(lead, rate: float, n: int, code_psl7):
-    """p50/p99 latency of single-syndrome requests on the continuous-batching server: Poisson
-    arrivals, 70 % PSL(2,7) / 30 % PSL(2,11), depolarizing p = 0.03 (both sides decoded)."""
+def _serving(lead, rates, n: int, code_psl7, unloaded_n: int = 2000):
+    """Latency and throughput of single-syndrome requests on the continuous-batching server:
+    Poisson arrivals at each offered rate, 70 % PSL(2,7) / 30 % PSL(2,11), depolarizing p = 0.03
+    (both sides decoded); then the unloaded latency: requests 1 ms apart, so each one is alone on
+    the device (a batch of one)."""
     import numpy as np
     import workloads
     from paper_2605_17796_gb300 import serving as sv
     code11 = lead.Code.from_instance(workloads.standard("PSL(2,11)", 0)).prepare(code_psl7.info.prepared_device)
     codes = [code_psl7, code11]
     p = 0.03
-    rng = np.random.default_rng(0)
-    arrival, code_of = sv.poisson_trace(rate, n, [0.7, 0.3], rng)
-    rows = [sv.request_rows(c, p, int((code_of == i).sum()), seed=100 + i) for i, c in enumerate(codes)]
     srv = lead.Server(codes, [2 * p / 3] * 2, max_batch=256, streams=6, budget_bytes=2 << 30)
-    # warm-up: a short trace so every kernel is loaded before the measured one
-    warm_arr, warm_code = sv.poisson_trace(rate, 2000, [0.7, 0.3], np.random.default_rng(1))
+    # warm-up: a short trace so every kernel is loaded before the measured ones
+    warm_arr, warm_code = sv.poisson_trace(rates[0], 2000, [0.7, 0.3], np.random.default_rng(1))
     warm_rows = [sv.request_rows(c, p, int((warm_code == i).sum()), seed=200 + i) for i, c in enumerate(codes)]
     sv.run_trace(srv, warm_rows, warm_arr, warm_code)
+    runs = []
+    for k, rate in enumerate(rates):
+        rng = np.random.default_rng(k)
+        arrival, code_of = sv.poisson_trace(rate, n, [0.7, 0.3], rng)
+        rows = [sv.request_rows(c, p, int((code_of == i).sum()), seed=100 + 10 * k + i) for i, c in enumerate(codes)]
+        res, _ = sv.run_trace(srv, rows, arrival, code_of)
+        runs.append(sv.latency_stats(res, rate))
+    # unloaded: evenly spaced requests 1 ms apart
+    code_of = np.random.default_rng(7).choice(2, size=unloaded_n, p=[0.7, 0.3]).astype(np.int32)
+    arrival = (np.arange(unloaded_n, dtype=np.int64) * 1_000_000)
+    rows = [sv.request_rows(c, p, int((code_of == i).sum()), seed=300 + i) for i, c in enumerate(codes)]
     res, _ = sv.run_trace(srv, rows, arrival, code_of)
+    unloaded = sv.latency_stats(res, 1000.0)
+    unloaded["per_code"] = {name: {"p50_us": float(np.percentile(((res["done_ns"] - res["arrival_ns"]) / 1e3)[res["code"] == i], 50)),
+                                   "p99_us": float(np.percentile(((res["done_ns"] - res["arrival_ns"]) / 1e3)[res["code"] == i], 99))}
+                            for i, name in enumerate(("PSL(2,7)", "PSL(2,11)"))}
     srv.close()
-    out = sv.latency_stats(res, rate)
-    out.update({"mix": "70% PSL(2,7) / 30% PSL(2,11)", "noise": "depolarizing p=0.03, both sides",
-                "max_batch": 256, "streams": 6})
+    return {"runs": runs, "unloaded": unloaded, "mix": "70% PSL(2,7) / 30% PSL(2,11)",
+            "noise": "depolarizing p=0.03, both sides", "max_batch": 256, "streams": 6}
+
+
+def _prior_local(lead, code, tc_peak_tflops: float, shots: int = 1 << 15, p: float = 0.02):
+    """Phase 1 under per-qubit priors (p_i uniform on [p/2, 3p/2]) on the sweep's code: vertex
+    items per second of lead_local_estimate_priors (prior LLRs, local posteriors, merge) with the
+    tensor-core kernel and with the CUDA-core kernel, CUDA events around each call. The tensor
+    cores compute 2 terms x 2 x (Delta 2^kB) x NK multiply-adds per item for each of the two
+    contractions (K1 = 48, NK = 512 on this code)."""
+    import torch
+    info = code.info
+    sz = torch.zeros((shots, info.words_m[0]), dtype=torch.int32, device="cuda")
+    ex = torch.zeros((shots, info.words_n), dtype=torch.int32, device="cuda")
+    code.sample(lead.NOISE_X, p, shots, 11, 0, err_x=ex, syn_z=sz)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    prior = torch.rand((shots, info.n), generator=g, device="cuda") * p + 0.5 * p
+    lam = torch.zeros((shots, info.n), dtype=torch.float32, device="cuda")
+    o = lead.opts(side=0, p=p)
+    ws = torch.zeros(code.priors_workspace_bytes(o, shots) // 4 + 64, dtype=torch.int32, device="cuda")
+    out = {"shots": shots, "p_range": [0.5 * p, 1.5 * p]}
+    for name, simt in (("tensor_cores", "0"), ("cuda_cores", "1")):
+        os.environ["LEAD_PRIOR_SIMT"] = simt
+        code.local_estimate_priors(o, sz, shots, prior, lam, workspace=ws)       # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            code.local_estimate_priors(o, sz, shots, prior, lam, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        out[name] = {"items_per_s": shots * info.order / (ms / 1e3), "shots_per_s": shots / (ms / 1e3)}
+    os.environ.pop("LEAD_PRIOR_SIMT", None)
+    flops = 2 * 2 * 2 * (info.delta * 8) * 512            # two contractions, two terms, 2 flops per MAC
+    tc = out["tensor_cores"]["items_per_s"] * flops / 1e12
+    out["tensor_contraction"] = {"flops_per_item": flops, "achieved_tflops": tc, "peak_tflops": tc_peak_tflops,
+                                 "frac": tc / tc_peak_tflops,
+                                 "note": "whole call timed (prior LLRs, CUDA-core log-sums, least-cost search, merge)"}
     return out
+
+
+def _compare_with_oracle(lead, code, pipe, decode, out_dir: str, procs: int, shots_per_p: int):
+    """The GPU's outputs for the shots the oracle children decoded (seed 0, shots
+    0 .. procs * shots_per_p - 1 at every p): the number of shots whose status, iteration count
+    or correction differs from the oracle's."""
+    import numpy as np
+    info = code.info
+    n_sh = procs * shots_per_p
+    words = (info.n + 31) // 32
+    mism = 0
+    for pi, p in enumerate(P_SWEEP):
+        code.sample(lead.NOISE_X, p, n_sh, 0, 0, err_x=pipe.err[0], syn_z=pipe.syn[0])
+        decode(lead.opts(side=0, p=p), pipe.syn[0], n_sh, pipe.corr[0], pipe.status[0], pipe.iters[0],
+               workspace=pipe.workspace)
+        corr = pipe.corr[0][:n_sh].cpu().numpy().view(np.uint32)
+        st = pipe.status[0][:n_sh].cpu().numpy()
+        it = pipe.iters[0][:n_sh].cpu().numpy()
+        for i in range(procs):
+            z = np.load(os.path.join(out_dir, f"oracle_{i}.npz"))
+            sl = slice(i * shots_per_p, (i + 1) * shots_per_p)
+            bad = ((z[f"status{pi}"] != st[sl]) | (z[f"iters{pi}"] != it[sl]) |
+                   (z[f"corr{pi}"] != corr[sl, :words]).any(axis=1) | (corr[sl, words:] != 0).any(axis=1))
+            mism += int(bad.sum())
+    return mism, n_sh * len(P_SWEEP)
+
+
+def _minsum_baseline(lead, pipe, sink, shots_per_p: int):
+    """The plain global min-sum baseline (use_lead = 0: channel prior, same iteration cap) on the
+    same shots as the first timed LEAD step: per p, decode shots/s (CUDA events around the decode
+    calls), logical error rate with its Wilson interval and mean iterations."""
+    import torch
+    from paper_2605_17796_gb300 import replicas
+    out = {}
+    tot_ms, tot = 0.0, 0
+    for pi, p in enumerate(P_SWEEP):
+        off = replicas.shot_offset(0, 0, 1, pi, len(P_SWEEP), shots_per_p)
+        sink[0] = []
+        r = pipe.run(lead.NOISE_X, p, shots_per_p, seed=0, offset=off, use_lead=False)
+        torch.cuda.synchronize()
+        ms = sum(e0.elapsed_time(e1) for e0, e1, _ in sink[0])
+        sink[0] = None
+        tot_ms += ms
+        tot += shots_per_p
+        out[f"{p:.2f}"] = {"decode_shots_per_s": shots_per_p / (ms / 1e3), "ler": r.failures / shots_per_p,
+                           "ler_ci95": wilson95(r.failures, shots_per_p), "mean_iters": r.iters_sum / shots_per_p}
+    return {"shots_per_p": shots_per_p, "decode_shots_per_s": tot / (tot_ms / 1e3), "per_p": out}
 
 
 from paper_2605_17796_gb300.stats import wilson95  # noqa: E402
@@ -251,11 +360,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shots-per-p", type=int, default=1_000_000)
     ap.add_argument("--chunk", type=int, default=1 << 20)
-    ap.add_argument("--oracle-shots-per-p", type=int, default=3)
+    ap.add_argument("--oracle-shots-per-p", type=int, default=3,
+                    help="reference arm: oracle shots per p per process and step")
+    ap.add_argument("--baseline-shots-per-p", type=int, default=100,
+                    help="cpu_baseline leg: oracle shots per p per process (about 30 s of decoding)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--oracle-child", nargs=3, type=int)
-    ap.add_argument("--serving-rate", type=float, default=1e5)
+    ap.add_argument("--oracle-child", nargs="+")
+    ap.add_argument("--serving-rates", type=float, nargs="+", default=[1e5, 3e5, 1e6])
     ap.add_argument("--serving-requests", type=int, default=30000)
+    ap.add_argument("--minsum-shots-per-p", type=int, default=1_000_000)
+    ap.add_argument("--no-minsum", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--precision-shots", type=int, default=1_000_000)
     ap.add_argument("--no-modes", action="store_true")
@@ -263,7 +377,8 @@ def main():
     args = ap.parse_args()
 
     if args.oracle_child:
-        _oracle_child(*args.oracle_child)
+        a = args.oracle_child
+        _oracle_child(int(a[0]), int(a[1]), int(a[2]), a[3] if len(a) > 3 else "")
         return
 
     rank = int(os.environ.get("RANK", "0"))
@@ -317,6 +432,7 @@ def main():
     # ---- per-kernel CUDA-event timing of the decode call inside the timed region -------------
     decode_events = []
     orig_decode = code.decode
+    sink = [None]          # the list that records (start, end, shots) of each decode call, or None
 
     def timed_decode(*a, **k):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -324,10 +440,9 @@ def main():
         e0.record(stream)
         orig_decode(*a, **k)
         e1.record(stream)
-        if timing_on[0]:
-            decode_events.append((e0, e1, a[2]))
+        if sink[0] is not None:
+            sink[0].append((e0, e1, a[2]))
 
-    timing_on = [False]
     code.decode = timed_decode
 
     results = {}
@@ -344,11 +459,11 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    clk_dir = tempfile.mkdtemp(prefix="lead_bench_")
+    clk_path = os.path.join(clk_dir, f"clocks_rank{rank}.csv")
     sampler = _clock_sampler(clk_path) if local_rank == 0 else None
     time.sleep(0.3)
-    timing_on[0] = True
+    sink[0] = decode_events
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -357,7 +472,7 @@ def main():
     sweep = sweeps[-1]
     ev1.record(stream)
     torch.cuda.synchronize()
-    timing_on[0] = False
+    sink[0] = None
     if world > 1:
         torch.distributed.barrier()
     if sampler:
@@ -375,7 +490,7 @@ def main():
     # decode kernel time inside the timed region
     dec_ms = sum(e0.elapsed_time(e1) for e0, e1, _ in decode_events)
     chunks_per_p = -(-args.shots_per_p // args.chunk)
-    launches_per_chunk = 4          # sample, local table, min-sum decode, check
+    launches_per_chunk = 5          # sample, local table, class tables, min-sum decode, check
     gpu_launches = args.steps * len(P_SWEEP) * chunks_per_p * launches_per_chunk
 
     # ---- e2e: host syndromes and errors in pinned memory -> decode -> corrections back ------
@@ -431,35 +546,50 @@ def main():
     H = code.check_matrix(0)
     E = int(H.sum())
     # algorithmic work of flooding min-sum per edge and iteration: v2c subtract, |.|, two
-    # compares (min1/min2), sign parity, posterior add = 6 ops; plus one prior evaluation per slot
-    ops = 6.0 * E * iters_total + 0.0
+    # compares (min1/min2), sign parity, posterior add = 6 ops. Three of them (the compares and
+    # the parity bit operation) issue on the ALU pipe, 64 lanes per SM (16 per sub-partition);
+    # the other three on the FMA pipe, 128 lanes per SM. The ALU pipe binds: 64/3 edges per
+    # SM-cycle = 128 algorithmic ops per SM-cycle.
+    ops = 6.0 * E * iters_total
     clock_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * clock_mhz * 1e6 / 1e12         # Tops/s: 128 FP32/INT lanes per SM
+    alu_peak = 152 * 128 * clock_mhz * 1e6 / 1e12         # Tops/s
     achieved = ops / (dec_ms / 1e3) / 1e12 if dec_ms > 0 else None
-    roofline = {"kernel": "bp_kernel (fused local estimation + merge + min-sum)", "bound": "alu",
+    roofline = {"kernel": "lead_bp_jit (fused local estimation lookup + merge + min-sum)", "bound": "alu",
                 "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                 "frac": (achieved / alu_peak) if achieved else None, "traffic": None,
-                "peak_source": f"derived: 152 SMs x 128 lanes x {clock_mhz:.0f} MHz",
+                "peak_source": (f"derived: 152 SMs x {clock_mhz:.0f} MHz x 128 ops per SM-cycle; 6 ops per edge "
+                                f"and iteration, 3 on the ALU pipe (64 lanes per SM, binding: 64/3 edges per "
+                                f"SM-cycle) and 3 on the FMA pipe (128 lanes per SM)"),
+                "work_per_unit": f"6 ops x {E} edges per shot-iteration; {iters_total} shot-iterations",
                 "decode_ms_in_timed_region": dec_ms}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         procs = _host_cores()
-        r = _run_oracle(args.oracle_shots_per_p, 0, 0, procs)
+        out_dir = tempfile.mkdtemp(prefix="lead_oracle_")
+        r = _run_oracle(args.baseline_shots_per_p, 0, 0, procs, out_dir=out_dir)
+        mism, compared = _compare_with_oracle(lead, code, pipe, orig_decode, out_dir, procs, args.baseline_shots_per_p)
         cpu = {"value": r["shots"] / r["seconds"], "unit": UNIT, "cores": procs, "kind": "oracle",
                "per_core": r["per_core"],
-               "sample": f"{procs} single-threaded numpy processes x {args.oracle_shots_per_p} shots per p "
-                         f"x 10 p values on disjoint shots ({r['shots']} shots, {r['seconds']:.1f} s wall)"}
+               "sample": f"{procs} single-threaded numpy processes x {args.baseline_shots_per_p} shots per p "
+                         f"x 10 p values on disjoint shots ({r['shots']} shots, {r['seconds']:.1f} s wall)",
+               "mismatches": mism, "compared_shots": compared,
+               "compared": "status, iterations and correction of every oracle shot against the GPU's"}
 
-    local_est = precision = iterated = None
+    minsum = None
+    if not args.no_minsum and world == 1:
+        minsum = _minsum_baseline(lead, pipe, sink, args.minsum_shots_per_p)
+
+    local_est = precision = iterated = prior_local = None
     if not args.no_modes and world == 1:
         local_est = _local_estimation(lead, code, pipe, peaks["hbm_gbs"], min(args.chunk, 1 << 20))
+        prior_local = _prior_local(lead, code, peaks.get("bf16_tflops", 1900.0))
         precision = _precision_modes(lead, pipe, args.precision_shots)
         iterated = _iterated_lead(lead, pipe, min(args.iterated_shots, args.chunk))
 
     serving = None
     if not args.no_serving and world == 1:
-        serving = _serving(lead, args.serving_rate, args.serving_requests, code)
+        serving = _serving(lead, args.serving_rates, args.serving_requests, code)
 
     clocks = _clock_summary(clk_path, dev)
     ler = {f"{p:.2f}": f / n for p, f, n in zip(P_SWEEP, sweep_fail, sweep_shots)}
@@ -473,7 +603,8 @@ def main():
                        "l2": "inputs larger than L2 (2^20-shot chunks, 400 MB of errors)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-            "local_estimation": local_est,
+            "minsum_baseline": minsum,
+            "local_estimation": local_est, "prior_local": prior_local,
             "precision_modes": ({"p": 0.05, "shots": args.precision_shots, "modes": precision}
                                 if precision else None),
             "iterated_lead": ({"shots": min(args.iterated_shots, args.chunk), "runs": iterated}

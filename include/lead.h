@@ -196,10 +196,26 @@ int lead_sample(const lead_code* code, int32_t noise, double p, int64_t shots, u
                 uint64_t shot_offset, uint32_t* err_x, uint32_t* err_z, uint32_t* syn_z,
                 uint32_t* syn_x, void* stream);
 
+/*
+ * lead_prior_llr -- the prior LLR of Phase 2, lambda(p) = ln((1 - p)/p), for n binary32
+ * probabilities (p clamped to [2^-23, 1 - 2^-23]): llr[i] = lambda(p[i]). It is the conversion
+ * every decode call applies to merged and channel probabilities. Evaluated in binary32 pairs
+ * (double-float arithmetic: TwoSum, Fast2Sum, exact products by fused multiply-add) from the
+ * series ln m = 2 artanh((m - 1)/(m + 1)) after reducing (1 - p)/p to 2^e m, m in
+ * [sqrt(1/2), sqrt(2)); accurate to about 2^-45 before the final rounding, so llr[i] is the
+ * binary32 rounding of the exact value except for inputs within that distance of a rounding
+ * boundary (3 of the 184 549 377 binary32 values in [2^-23, 1/2], each 1 ulp off). Odd about
+ * 1/2: lambda(1 - p) = -lambda(p) exactly, lambda(1/2) = 0.
+ *  p, llr (dev, n floats). n == 0 is a no-op. Errors: LEAD_EINVAL (n < 0, NULL pointers),
+ *  LEAD_ECUDA.
+ */
+int lead_prior_llr(const float* p, float* llr, int64_t n, void* stream);
+
 /* Bytes of device workspace lead_local_estimate / lead_decode need for these options
  * (16-byte aligned start required); 0 for the baseline (use_lead = 0). A multiple of 256.
- * lead_decode reads only the first 2^m_l * Delta^2 * 4 bytes (rounded up to 256): the local
- * posterior table; lead_local_estimate also uses the rest (class bytes and pair table). */
+ * Both calls write the local posterior table (2^m_l * Delta^2 floats, rounded up to 256 bytes)
+ * and then its class tables (the class byte of every entry and the prior LLR of every pair of
+ * distinct table values), and read them back. */
 size_t lead_workspace_bytes(const lead_code* code, const lead_decode_opts* opts, int64_t shots);
 
 /*
@@ -233,9 +249,8 @@ int lead_local_table_est(const lead_code* code, int32_t side, double p, int32_t 
 /*
  * lead_local_estimate -- Phases 1 and 2 (Algorithm 1): for every qubit i with views (v0, j0)
  * and (v1, j1) on the side, p_i = alpha * ((q(s_v0, j0) + q(s_v1, j1)) * 1/2) in binary32,
- * clamped to [2^-23, 1 - 2^-23], and llr[shot * n + i] = ln((1 - p_i)/p_i) in binary32 (by
- * linear interpolation in a 2817-node table over the binary32 exponent and top 7 fraction bits
- * of min(p, 1-p), error below 2e-5), then stored in the format of opts->precision:
+ * clamped to [2^-23, 1 - 2^-23], and llr[shot * n + i] = lambda(p_i) = ln((1 - p_i)/p_i) as
+ * lead_prior_llr evaluates it, then stored in the format of opts->precision:
  *   LEAD_PREC_FP32 float; LEAD_PREC_BF16 / LEAD_PREC_FP16 the 16-bit pattern (uint16) of the
  *   bfloat16 / binary16 rounding (to nearest even) of that binary32 value.
  *  syn (dev, shots x words_m[side]); llr (dev, shots x n elements of that format);
@@ -278,20 +293,22 @@ int lead_decode(const lead_code* code, const lead_decode_opts* opts, const uint3
  * counterpart; this entry point exists for callers that cannot allocate device memory: a
  * real-time error-correction loop whose decode deadline leaves no room for cudaMalloc (which
  * can block and synchronise the whole device), or an application whose own pool allocator owns
- * all device memory. The local posterior table that lead_decode keeps in the workspace lives
- * instead in one fixed device array of LEAD_NOALLOC_TABLE_BYTES bytes inside the library; every
- * GPU that loads the library holds that array until the process exits.
+ * all device memory. The per-call tables that lead_decode keeps in the workspace (the local
+ * posterior table and its class tables) live instead in one fixed device array of
+ * LEAD_NOALLOC_TABLE_BYTES bytes inside the library; every GPU that loads the library holds that
+ * array until the process exits.
  *  Arguments and results are those of lead_decode. The call allocates nothing (no cudaMalloc,
  *  no cudaFree, no allocating library routine).
- *  The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *  that device current; make that first call before any stream capture.
- *  All calls on a device share the array and it keeps the last call's table: calls whose device
+ *  The first call with shots > 0 on a device looks up the array's device address
+ *  (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ *  capture. shots == 0 returns LEAD_OK at once, as lead_decode does.
+ *  All calls on a device share the array and it keeps the last call's tables: calls whose device
  *  work overlaps (other streams, or concurrent host threads) race on it and must be serialised
- *  by the caller. Each call rewrites the whole table before reading it.
- * Errors: those of lead_decode; LEAD_EINVAL also when the table (2^m_l * delta^2 floats) would
- * exceed LEAD_NOALLOC_TABLE_BYTES.
+ *  by the caller. Each call rewrites the tables before reading them.
+ * Errors: those of lead_decode; LEAD_EINVAL also when the tables would exceed
+ * LEAD_NOALLOC_TABLE_BYTES (local codes with more than 2^10 local syndromes or 36 positions).
  */
-#define LEAD_NOALLOC_TABLE_BYTES 147456   /* 2^10 local syndromes x 36 floats */
+#define LEAD_NOALLOC_TABLE_BYTES 444928   /* table of 2^10 x 36 floats + class bytes + 255^2 pairs */
 int lead_decode_noalloc(const lead_code* code, const lead_decode_opts* opts, const uint32_t* syn,
                         int64_t shots, uint32_t* corr, uint8_t* status, int32_t* iters,
                         float* llr, void* stream);
@@ -423,9 +440,11 @@ int lead_check(const lead_code* code, int32_t side, const uint32_t* err, const u
  * shots whenever a stream slot is free, and keeps up to `streams` batches in flight (their
  * kernels overlap on the device). Each slot owns device buffers for max_batch shots; the number
  * of slots is min(streams, budget_bytes / slot size) (admission by memory; LEAD_EOOM if not even
- * one fits). Every batch runs lead_decode on the sides in sides_mask and copies corrections and
- * statuses back; completion is detected with cudaEventQuery. A result does not depend on the
- * other requests of its batch (shots decode independently).
+ * one fits). lead_server_create builds, once, the Phase 1-2 tables of every code and side (the
+ * local posterior table for the code's p and its class tables, as lead_decode would); every
+ * batch then runs lead_decode's min-sum kernel on the sides in sides_mask with those tables and
+ * copies corrections and statuses back; completion is detected with cudaEventQuery. A result
+ * does not depend on the other requests of its batch (shots decode independently).
  */
 typedef struct lead_server lead_server;
 
@@ -478,6 +497,16 @@ const char* lead_status_string(int status);
  * tests out and never waits. This replaces a memory checker, which this build does not use.
  */
 #define LEAD_BUILD_CHECKED 1
+/*
+ * lead_code_device_errors -- device error flags of a code's kernels (host, synchronous: waits
+ * for the device). Bit 0 (LEAD_DEVERR_TC_WAIT): a per-qubit-prior kernel's wait for its
+ * tensor-core operations ran out of its bound (the kernel stopped early and released its tensor
+ * memory; the outputs of that call are incomplete). clear != 0 resets the flags.
+ * Errors: LEAD_EINVAL, LEAD_ESTATE (not prepared, or another device current), LEAD_ECUDA.
+ */
+#define LEAD_DEVERR_TC_WAIT 1
+int lead_code_device_errors(const lead_code* code, uint32_t* flags, int32_t clear);
+
 /* LEAD_BUILD_* flags of the loaded library. */
 int lead_build_flags(void);
 /* The last failed check of a code, as {failures, site, index, bound}; all zero if none. */

@@ -17,7 +17,8 @@ Phase 3 (global decoder): flooding min-sum with scaling 1 and at most ``max_iter
 
 Two numeric tracks:
 * ``prior_f64``: q, p_i and the LLR in FP64 -- the quantities the single-precision path must
-  reproduce within its tolerance;
+  reproduce within its tolerance; ``decode_f64`` continues it with min-sum in FP64 (same rules
+  and order), the reference for how often binary32 rounding changes a decision;
 * the decision track in IEEE binary32 (``prior_f32`` and ``min_sum``), because floating point
   decides the hard decisions: q rounded to binary32, the boost and merge in binary32, the LLR
   by ``local.llr_f32``; min-sum messages in binary32 with this fixed order of additions:
@@ -202,25 +203,29 @@ def _syndrome_of(H: np.ndarray, e: np.ndarray) -> np.ndarray:
 
 
 def min_sum(H: np.ndarray, block: int, syn: np.ndarray, llr: np.ndarray, max_iter: int = 32,
-            early_stop: bool = True, precision: int = PREC_FP32):
+            early_stop: bool = True, precision: int = PREC_FP32, dtype=np.float32):
     """Phase 3, flooding min-sum in binary32 on the check matrix H whose rows come in blocks of
     ``block`` (one block per vertex view; the order of additions is documented in the module
     doc). syn (S, m) 0/1, llr (S, n) float32 -> (corr (S, n) uint8, status (S,) uint8,
     iters (S,) int32, post (S, n) float32 final posterior LLRs).
     ``early_stop=False`` runs all ``max_iter`` iterations and reports the last decision (used to
     pin the message rules against the fixed point on cycle-free graphs). ``precision`` selects
-    the storage format of the module doc."""
+    the storage format of the module doc. ``dtype=np.float64`` runs the same rules and order in
+    binary64 (the FP64 reference track; posteriors are then returned in binary64)."""
+    ft = np.dtype(dtype).type
+    if ft is np.float64 and precision != PREC_FP32:
+        raise ValueError("storage modes are defined on the binary32 track")
     R = lambda x: round_storage(x, precision)  # noqa: E731
     g = _Graph(H, block)
     S, n = llr.shape
-    lam = R(llr.astype(np.float32))
+    lam = R(llr.astype(ft))
     corr = np.zeros((S, n), dtype=np.uint8)
     status = np.zeros(S, dtype=np.uint8)
     iters = np.zeros(S, dtype=np.int32)
-    post_out = np.zeros((S, n), dtype=np.float32)
+    post_out = np.zeros((S, n), dtype=ft)
     active = np.arange(S)
     dmax = g.nbr.shape[1]
-    c2v = np.zeros((S, g.m, dmax), dtype=np.float32)
+    c2v = np.zeros((S, g.m, dmax), dtype=ft)
     post = lam.copy()
     sgn_s = syn.astype(bool)
     edge_ok = g.edge >= 0
@@ -229,31 +234,31 @@ def min_sum(H: np.ndarray, block: int, syn: np.ndarray, llr: np.ndarray, max_ite
         if t > 0:
             # check-node update for the active shots
             pa = post[active]
-            v2c = (pa[:, g.nbr] - c2v[active]).astype(np.float32)
-            mag = np.where(g.valid[None], np.abs(v2c), np.float32(np.inf)).astype(np.float32)
+            v2c = (pa[:, g.nbr] - c2v[active]).astype(ft)
+            mag = np.where(g.valid[None], np.abs(v2c), ft(np.inf)).astype(ft)
             neg = np.signbit(v2c) & g.valid[None]
             # min over the other slots of a check = min(prefix minimum before k, suffix after k)
-            inf = np.full(mag.shape[:2] + (1,), np.inf, dtype=np.float32)
+            inf = np.full(mag.shape[:2] + (1,), np.inf, dtype=ft)
             pre = np.concatenate([inf, np.minimum.accumulate(mag, axis=2)[:, :, :-1]], axis=2)
             suf = np.concatenate([np.minimum.accumulate(mag[:, :, ::-1], axis=2)[:, :, ::-1][:, :, 1:],
                                   inf], axis=2)
             mn = R(np.minimum(pre, suf))
             # parity of the other slots' signs = parity of all of them XOR the slot's own sign
             par = ((neg.sum(axis=2) & 1).astype(bool)[:, :, None] ^ neg) ^ sgn_s[active][:, :, None]
-            new = np.where(par, -mn, mn).astype(np.float32)
-            new = np.where(g.valid[None], new, np.float32(0.0)).astype(np.float32)
+            new = np.where(par, -mn, mn).astype(ft)
+            new = np.where(g.valid[None], new, ft(0.0)).astype(ft)
             c2v[active] = new
             # variable-node update: per-block sums in increasing row, blocks in increasing order
             flat = new.reshape(new.shape[0], -1)
             acc = lam[active].copy()
             for tb in range(g.edge.shape[1]):
-                U = np.zeros((active.size, n), dtype=np.float32)
+                U = np.zeros((active.size, n), dtype=ft)
                 for u in range(g.edge.shape[2]):
                     ok = edge_ok[:, tb, u]
-                    vals = np.where(ok[None], flat[:, edge_ix[:, tb, u]], np.float32(0.0))
-                    U = (U + vals).astype(np.float32)
+                    vals = np.where(ok[None], flat[:, edge_ix[:, tb, u]], ft(0.0))
+                    U = (U + vals).astype(ft)
                 has = edge_ok[:, tb, 0]
-                acc = np.where(has[None], (acc + R(U)).astype(np.float32), acc).astype(np.float32)
+                acc = np.where(has[None], (acc + R(U)).astype(ft), acc).astype(ft)
             post[active] = R(acc)
         e = (post[active] < 0).astype(np.uint8)
         ok = (_syndrome_of(g.H, e) == syn[active]).all(axis=1)
@@ -286,6 +291,19 @@ def decode(code: TannerCode, side_id: int, syn: np.ndarray, p: float, alpha: flo
         lam = channel_prior_f32(code.n, syn.shape[0], p)
     side = code.sides[side_id]
     return min_sum(side.H, side.m_l, syn, lam, max_iter, precision=precision)
+
+
+def decode_f64(code: TannerCode, side_id: int, syn: np.ndarray, p: float, alpha: float = 1.0,
+               max_iter: int = 32, use_lead: bool = True):
+    """Algorithm 1 on the FP64 track: the prior LLRs of ``prior_f64`` (or the channel LLR
+    ln((1-p)/p) in binary64 for use_lead=False) and min-sum in binary64 with the same rules and
+    order. It measures how often the binary32 decision track decides differently."""
+    if use_lead:
+        _, lam = prior_f64(code, side_id, syn, p, alpha)
+    else:
+        lam = np.full((syn.shape[0], code.n), np.log((1.0 - p) / p))
+    side = code.sides[side_id]
+    return min_sum(side.H, side.m_l, syn, lam, max_iter, dtype=np.float64)
 
 
 def redecode(code: TannerCode, side_id: int, syn: np.ndarray, post: np.ndarray, alpha: float = 1.0,

@@ -53,7 +53,14 @@ def _poly_mul(a: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 def _row_tables(RB: np.ndarray):
     """For every row pattern x in F_2^Delta (bit b = x_b): f = R_B x as an integer (bit rB),
-    its weight, and the per-(f) polynomials P(f)[w] and P_b(f)[w]."""
+    its weight, and the per-(f) polynomials P(f)[w] and P_b(f)[w] (cached per R_B)."""
+    RB = np.ascontiguousarray(RB, dtype=np.uint8)
+    return _row_tables_cached(RB.tobytes(), RB.shape)
+
+
+@functools.lru_cache(maxsize=16)
+def _row_tables_cached(rb_bytes, rb_shape):
+    RB = np.frombuffer(rb_bytes, dtype=np.uint8).reshape(rb_shape)
     kB, delta = RB.shape
     xs = np.arange(1 << delta)
     bits = (xs[:, None] >> np.arange(delta)[None, :]) & 1          # (2^Delta, Delta)
@@ -284,44 +291,61 @@ def macwilliams_zero_coset(L: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------------------
 # Single-precision decision path. Floating point decides the hard decisions of the global
 # decoder, so the oracle evaluates the prior LLR that feeds it in IEEE binary32 with a fixed
-# operation order, exactly as a single-precision implementation must:
+# operation order, as any single-precision implementation must:
 #   * boost and merge in binary32, p clamped to [2^-23, 1 - 2^-23];
-#   * lambda(p) = ln((1 - p)/p) by linear interpolation in a table over p in [2^-23, 1/2]:
-#     node i is the binary32 number with bit pattern (i + 13312) << 16 (the exponent and the
-#     top 7 fraction bits of p), T0[i] = lambda at node i, T1[i] = slope to node i + 1, and
-#     lambda = T0[i] + (p - p_i) * T1[i] (p - p_i is exact); for p > 1/2, lambda(p) = -lambda(1-p)
-#     (1 - p is exact there). Interpolation error <= (p/128)^2 / (8 p^2) ~ 7.6e-6.
-#   * the table entries are computed in binary64 from a logarithm evaluated by the inverse
-#     hyperbolic tangent series ln m = 2 atanh((m-1)/(m+1)) (Abramowitz & Stegun 4.1.27) with
-#     explicit operations, then rounded to binary32, so any implementation following the same
-#     steps obtains the same table bit for bit.
+#   * lambda(p) = ln((1 - p)/p) is the binary32 rounding (to nearest, ties to even) of the exact
+#     value: the plain definition. It is computed as 2 artanh(1 - 2p) in binary64 (an identity
+#     for ln((1-p)/p); 1 - 2p is exact in binary64 for binary32 p), whose relative error is a few
+#     2^-53; where that value lies so close to a binary32 rounding boundary that the error could
+#     decide the rounding, the exact value is compared with the boundary in 60-digit decimal
+#     arithmetic instead.
 # ---------------------------------------------------------------------------------------
 
-LN2_D = np.array([0x3FE62E42FEFA39EF], dtype=np.uint64).view(np.float64)[0]     # nearest double to ln 2
-SQRT2_D = np.array([0x3FF6A09E667F3BCD], dtype=np.uint64).view(np.float64)[0]   # nearest double to sqrt 2
 P_MIN_F = np.float32(2.0 ** -23)
 P_MAX_F = np.float32(1.0 - 2.0 ** -23)
-LLR_NODE0 = 13312                   # (2^-23 bit pattern) >> 16
-LLR_NODES = 2817                    # nodes 2^-23 ... 1/2
 
 
-def log_series_f64(x: np.ndarray) -> np.ndarray:
-    """ln x for positive normal binary64 x: x = 2^e m, m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh z
-    with z = (m - 1)/(m + 1), series through z^25 (error below 1e-16 for |z| <= 0.1716)."""
-    x = np.asarray(x, dtype=np.float64)
-    bits = x.view(np.uint64)
-    e = ((bits >> np.uint64(52)) & np.uint64(0x7FF)).astype(np.int64) - 1023
-    m = ((bits & np.uint64(0x000FFFFFFFFFFFFF)) | np.uint64(0x3FF0000000000000)).view(np.float64)
-    big = m > SQRT2_D
-    m = np.where(big, m * 0.5, m)
-    e = e + big.astype(np.int64)
-    z = (m - 1.0) / (m + 1.0)
-    w = z * z
-    s = np.full(x.shape, 2.0 / 25.0)
-    for k in range(23, 0, -2):
-        s = s * w
-        s = s + 2.0 / k
-    return e.astype(np.float64) * LN2_D + z * s
+def _llr_exact_round(p: float) -> np.float32:
+    """Binary32 rounding of ln((1-p)/p) for one binary32 p, decided in decimal arithmetic: the
+    two binary32 neighbours of the binary64 estimate bracket the exact value, and the exact value
+    is compared with their midpoint (p and every binary32 number are exact decimals)."""
+    import decimal
+    ctx = decimal.Context(prec=60)
+    dp = decimal.Decimal(float(p))
+    exact = ctx.ln(ctx.divide(ctx.subtract(decimal.Decimal(1), dp), dp))
+    est = np.float32(float(exact))
+    lo = np.nextafter(est, np.float32(-np.inf), dtype=np.float32)
+    hi = np.nextafter(est, np.float32(np.inf), dtype=np.float32)
+    best = est
+    for cand in (lo, hi):          # the nearest of the three; ties to the even significand
+        dc = abs(ctx.subtract(decimal.Decimal(float(cand)), exact))
+        db = abs(ctx.subtract(decimal.Decimal(float(best)), exact))
+        if dc < db or (dc == db and (int(np.float32(cand).view(np.uint32)) & 1) == 0):
+            best = cand
+    return np.float32(best)
+
+
+def llr_f32(p: np.ndarray) -> np.ndarray:
+    """lambda = ln((1 - p)/p) for binary32 p clamped to [2^-23, 1 - 2^-23], rounded to binary32
+    (see the block comment above)."""
+    p = np.clip(np.asarray(p, dtype=np.float32), P_MIN_F, P_MAX_F)
+    y = 2.0 * np.arctanh(1.0 - 2.0 * p.astype(np.float64))
+    lam = y.astype(np.float32)
+    # distance of y from the rounding boundary next to lam, against 2^-49 |y| (well above the
+    # binary64 error of artanh and of the doubling): only there can the rounding be in doubt
+    al = np.abs(lam)
+    a = al.astype(np.float64)
+    half_up = (np.nextafter(al, np.float32(np.inf), dtype=np.float32).astype(np.float64) - a) / 2.0
+    half_dn = (a - np.nextafter(al, np.float32(0), dtype=np.float32).astype(np.float64)) / 2.0
+    d = np.abs(y - lam.astype(np.float64))
+    tol = 2.0 ** -49 * np.abs(y)
+    doubt = (np.abs(d - half_up) <= tol) | (np.abs(d - half_dn) <= tol)
+    if doubt.any():
+        flat_p, flat_l, flat_d = p.reshape(-1), lam.reshape(-1), doubt.reshape(-1)
+        for k in np.nonzero(flat_d)[0]:
+            flat_l[k] = _llr_exact_round(flat_p[k])
+        lam = flat_l.reshape(p.shape)
+    return lam.astype(np.float32)
 
 
 # Cody-Waite split of ln 2 (the fdlibm pair): LN2_HI has its low 21 bits zero (32 significant
@@ -381,36 +405,6 @@ def flip_prob_f32(post: np.ndarray) -> np.ndarray:
     return (np.float32(1.0) / (np.float32(1.0) + e).astype(np.float32)).astype(np.float32)
 
 
-def llr_tables():
-    """(T0, T1) binary32 node values and slopes of lambda(p) = ln((1 - p)/p) on [2^-23, 1/2]."""
-    i = np.arange(LLR_NODES + 1, dtype=np.uint32)
-    pn = ((i + np.uint32(LLR_NODE0)) << np.uint32(16)).view(np.float32).astype(np.float64)
-    lam = log_series_f64(1.0 - pn) - log_series_f64(pn)
-    T0 = lam[:LLR_NODES].astype(np.float32)
-    T1 = ((lam[1:] - lam[:-1]) / (pn[1:] - pn[:-1])).astype(np.float32)
-    T1[LLR_NODES - 1] = np.float32(0.0)            # the node p = 1/2 is only used with p - p_i = 0
-    return T0, T1
-
-
-_LLR_T = None
-
-
-def llr_f32(p: np.ndarray) -> np.ndarray:
-    """lambda = ln((1 - p)/p) on the binary32 decision track (see the block comment above)."""
-    global _LLR_T
-    if _LLR_T is None:
-        _LLR_T = llr_tables()
-    T0, T1 = _LLR_T
-    p = np.clip(np.asarray(p, dtype=np.float32), P_MIN_F, P_MAX_F).astype(np.float32)
-    hi = p > np.float32(0.5)
-    q = np.where(hi, (np.float32(1.0) - p).astype(np.float32), p).astype(np.float32)
-    idx = (q.view(np.uint32) >> np.uint32(16)).astype(np.int64) - LLR_NODE0
-    node = ((idx + LLR_NODE0).astype(np.uint32) << np.uint32(16)).view(np.float32)
-    d = (q - node).astype(np.float32)
-    lam = (T0[idx] + (d * T1[idx]).astype(np.float32)).astype(np.float32)
-    return np.where(hi, -lam, lam).astype(np.float32)
-
-
 def boosted_table_f32(N, N1, ml_mask, p: float) -> np.ndarray:
     """Phase-1 output table in binary32: q rounded to binary32, then max(q, 1/2) on the bits of
     the ML decision (the boost of Algorithm 1; the ML member always satisfies H_v e = s_v)."""
@@ -429,10 +423,24 @@ def boosted_table_f32(N, N1, ml_mask, p: float) -> np.ndarray:
 # decision), ties broken by the least row-major key as in the uniform case.
 # ---------------------------------------------------------------------------------------
 
-def coset_row_images(RA: np.ndarray, RB: np.ndarray, s: int):
-    """All row-image matrices F (as (Delta,) arrays of f_a) with R_A F = S, for syndrome s."""
+@functools.lru_cache(maxsize=16)
+def _cosets_cached(ra_bytes, ra_shape, rb_bytes, rb_shape):
+    """The row-image matrices grouped by syndrome: (fa sorted by S = R_A F, start of each S)."""
+    RA = np.frombuffer(ra_bytes, dtype=np.uint8).reshape(ra_shape)
+    RB = np.frombuffer(rb_bytes, dtype=np.uint8).reshape(rb_shape)
     fa, s_of_F = _row_images(RA, RB)
-    return fa[:, s_of_F == s]
+    order = np.argsort(s_of_F, kind="stable")
+    starts = np.searchsorted(s_of_F[order], np.arange((1 << (ra_shape[0] * rb_shape[0])) + 1))
+    return fa[:, order], starts
+
+
+def coset_row_images(RA: np.ndarray, RB: np.ndarray, s: int):
+    """All row-image matrices F (as (Delta,) arrays of f_a) with R_A F = S, for syndrome s, in
+    increasing order of their packed value (the shot-invariant grouping is cached per local code)."""
+    RA = np.ascontiguousarray(RA, dtype=np.uint8)
+    RB = np.ascontiguousarray(RB, dtype=np.uint8)
+    fa, starts = _cosets_cached(RA.tobytes(), RA.shape, RB.tobytes(), RB.shape)
+    return fa[:, starts[s]:starts[s + 1]]
 
 
 def posterior_nonuniform(RA: np.ndarray, RB: np.ndarray, s: int, p: np.ndarray) -> np.ndarray:

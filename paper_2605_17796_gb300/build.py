@@ -21,10 +21,11 @@ LIB_CHECKED = os.path.join(HERE, "liblead_checked.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["device.cu", "sample.cu", "decode.cu", "priors.cu", "local.cu", "osd.cu", "iterated.cu"]
+CU_SOURCES = ["device.cu", "sample.cu", "decode.cu", "priors.cu", "prior_tc.cu", "local.cu", "osd.cu",
+              "iterated.cu"]
 CPP_SOURCES = ["code.cpp", "jit.cpp", "server.cpp"]
 # the run-time specialised min-sum kernel: these files are embedded (in this order) as text
-JIT_SOURCES = ["bp_jit_args.h", "lead_math.cuh", "bp_jit_kernel.cuh"]
+JIT_SOURCES = ["bp_jit_args.h", "lead_llr.cuh", "lead_math.cuh", "bp_jit_kernel.cuh"]
 CUDA_HOME = "/usr/local/cuda"
 
 
@@ -47,7 +48,9 @@ def _write_jit_source(build_dir: str = BUILD):
     parts = []
     for name in JIT_SOURCES:
         text = open(os.path.join(CSRC, name)).read()
-        text = "\n".join(line for line in text.splitlines() if line.strip() != "#pragma once")
+        # the files come concatenated in dependency order: drop the guards and the local includes
+        text = "\n".join(line for line in text.splitlines()
+                         if line.strip() != "#pragma once" and not line.startswith('#include "'))
         parts.append(f"// ---- {name}\n{text}\n")
     body = "".join(parts)
     if ")LEADJIT" in body:

@@ -13,7 +13,7 @@ struct BPJitArgs {
   int max_iter;       // global min-sum iterations
   int use_lead;       // 1: LEAD prior from the local table; 0: channel prior
   float alpha;        // Phase-2 scaling
-  double p;           // channel marginal (baseline prior)
+  float p;            // channel marginal (baseline prior), rounded to binary32
   long long shots;
   const unsigned int* syn;
   unsigned int* corr;
@@ -21,11 +21,12 @@ struct BPJitArgs {
   int* iters;
   float* llr;
   const float* table;           // 2^m_l x nl local posterior table (nullptr for the baseline)
+  const unsigned char* cls;     // class (distinct-value rank) of every table entry
+  const float* pair;            // K x K prior LLRs lambda(alpha (q_c0 + q_c1)/2) of class pairs
+  const int* header;            // header[0] = K; 0 means no class tables: merge from `table`
   const float* lam;             // shots x n per-qubit prior LLRs; when set, the prior of every slot
   const unsigned short* pa;     // [j][t] partner shared-memory address | first view << 15
   const unsigned short* views;  // [v][j] qubit index
-  const float* llr_t0;          // prior-LLR interpolation table: node values
-  const float* llr_t1;          //   and slopes
   unsigned long long* check;    // checked build: bounds-failure record {failures, site, index, bound}
 };
 

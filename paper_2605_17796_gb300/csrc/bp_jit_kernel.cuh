@@ -102,6 +102,19 @@ struct RowMag {
 // Shared-memory offset (bytes) of the word arrays behind the three NL x TS message arrays.
 constexpr unsigned int kMsgBytes = ((3u * LEAD_NL * LEAD_TS * (unsigned int)sizeof(msg_t)) + 15u) & ~15u;
 
+// Phases 1-2 for one slot: the merged prior LLR of the table entries e0 (this view) and e1 (the
+// partner view), lambda(alpha * ((q(e0) + q(e1)) * 1/2)). With K > 0 classes it is one lookup in
+// the K x K pair table the entry point built with the same arithmetic (bit-identical); otherwise
+// the merge is evaluated here.
+__device__ __forceinline__ float merged_prior(const lead::BPJitArgs& a, int K, int e0, int e1) {
+  if (K > 0) {
+    const int c0 = __ldg(a.cls + e0), c1 = __ldg(a.cls + e1);
+    const bool ok = lead::in_bounds(a.check, c0, K, 5) && lead::in_bounds(a.check, c1, K, 5);
+    return ok ? __ldg(a.pair + c0 * K + c1) : 0.0f;
+  }
+  return lead::merged_llr(__ldg(a.table + e0), __ldg(a.table + e1), a.alpha);
+}
+
 // New check-to-variable message of a local row of len positions to its k-th support position,
 // from the row's compressed state (m1, m2 magnitudes; meta = signs | argmin << 26 | parity << 31).
 __device__ __forceinline__ float c2v_msg(float m1, float m2, unsigned int meta, int k, int len) {
@@ -130,7 +143,8 @@ lead_bp_jit(const lead::BPJitArgs a) {
   const int tid = threadIdx.x;
   const int sl = tid / V, v = tid - sl * V;
   const bool lane_ok = tid < TS;
-  const float lam_ch = a.use_lead ? 0.0f : lead::channel_llr(a.p, a.llr_t0, a.llr_t1);
+  const float lam_ch = a.use_lead ? 0.0f : lead::channel_llr(a.p);
+  const int K = (a.use_lead && a.header) ? __ldg(a.header) : 0;   // classes of the local table
 
   for (long long g0 = (long long)blockIdx.x * spb; g0 < a.shots; g0 += (long long)gridDim.x * spb) {
     const int nsh = (int)((a.shots - g0) < spb ? (a.shots - g0) : spb);
@@ -161,8 +175,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
           const unsigned int jp = addr / TS, vp = addr - jp * TS - sl * V;
           const bool ok = lead::in_bounds(a.check, addr, NL * TS, 1) && lead::in_bounds(a.check, vp, V, 2);
           const unsigned int svp = ok ? lead::bit_field(srow, vp * ML, ML) : 0u;
-          lj = lead::merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp), a.alpha, a.llr_t0,
-                                a.llr_t1);
+          lj = merged_prior(a, K, sv * NL + j, svp * NL + jp);
         } else {
           lj = lam_ch;
         }
@@ -378,7 +391,8 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
 #pragma unroll
   for (int r = 0; r < C; ++r) ubase[r] = map_rank_generic(Us, r);
   const unsigned int flag0 = map_rank(flags, 0);
-  const float lam_ch = a.use_lead ? 0.0f : lead::channel_llr(a.p, a.llr_t0, a.llr_t1);
+  const float lam_ch = a.use_lead ? 0.0f : lead::channel_llr(a.p);
+  const int K = (a.use_lead && a.header) ? __ldg(a.header) : 0;   // classes of the local table
   const long long cid = blockIdx.x / C, ncl = gridDim.x / C;
 
   for (long long g0 = cid; g0 < a.shots; g0 += ncl) {
@@ -409,8 +423,7 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
           const bool ok = lead::in_bounds(a.check, addr, NL * TS, 1) && lead::in_bounds(a.check, pr, C, 4) &&
                           lead::in_bounds(a.check, vp, V, 2);
           const unsigned int svp = ok ? lead::bit_field(syn_s, vp * ML, ML) : 0u;
-          lj = lead::merged_llr(__ldg(a.table + sv * NL + j), __ldg(a.table + svp * NL + jp), a.alpha, a.llr_t0,
-                                a.llr_t1);
+          lj = merged_prior(a, K, sv * NL + j, svp * NL + jp);
         } else {
           lj = lam_ch;
         }

@@ -14,7 +14,6 @@ namespace lead {
 int check_device(const lead_code* code);
 int launch_table(const lead_code* code, int side, double p, float* table, cudaStream_t stream, int estimator,
                  int32_t* iters);
-size_t local_pair_extra_bytes(const lead_code* code, int side);
 int launch_local_pair(const lead_code* code, const lead_decode_opts* o, const uint32_t* syn, int64_t shots,
                       void* llr, const float* table, void* extra, cudaStream_t stream);
 
@@ -30,8 +29,6 @@ struct LocalArgs {
   const uint32_t* syn;
   const float* table;
   const uint32_t* qslots;
-  const float* llr_t0;
-  const float* llr_t1;
   void* llr;                    // float, or the 16-bit pattern of the storage format
 };
 
@@ -58,11 +55,8 @@ local_estimate_kernel(LocalArgs a, __grid_constant__ const SideParams P) {
   extern __shared__ __align__(16) uint32_t smem[];
   float* tab = reinterpret_cast<float*>(smem);
   const int tab_n = (1 << P.m_l) * NL;
-  // prior-LLR interpolation table staged once as (node value, slope) pairs: one 8-byte load
-  float2* tv = reinterpret_cast<float2*>(tab + tab_n + (tab_n & 1));
-  uint16_t* sv_s = reinterpret_cast<uint16_t*>(tv + kLlrNodes);   // [batch shot][vertex]
+  uint16_t* sv_s = reinterpret_cast<uint16_t*>(tab + tab_n);   // [batch shot][vertex]
   for (int i = threadIdx.x; i < tab_n; i += blockDim.x) tab[i] = __ldg(a.table + i);
-  for (int i = threadIdx.x; i < kLlrNodes; i += blockDim.x) tv[i] = make_float2(__ldg(a.llr_t0 + i), __ldg(a.llr_t1 + i));
   uint32_t vv[KQ], jj[KQ];       // (v0 | v1 << 16), (j0 | j1 << 16)
 #pragma unroll
   for (int k = 0; k < KQ; ++k) {
@@ -92,7 +86,7 @@ local_estimate_kernel(LocalArgs a, __grid_constant__ const SideParams P) {
         if (i < a.n) {
           const float q0 = tab[svr[vv[k] & 0xFFFFu] * NL + (jj[k] & 0xFFFFu)];
           const float q1 = tab[svr[vv[k] >> 16] * NL + (jj[k] >> 16)];
-          store_llr<PREC>(a.llr, row + i, merged_llr_s(q0, q1, a.alpha, tv));
+          store_llr<PREC>(a.llr, row + i, merged_llr(q0, q1, a.alpha));
         }
       }
     }
@@ -105,15 +99,24 @@ int bp_shots_per_block(const lead_code* code) {
   return std::max(1, 256 / code->order);
 }
 
-// The workspace lead_decode reads: the local posterior table (a multiple of 256 bytes).
-size_t decode_workspace_bytes(const lead_code* code, int side) {
+namespace {
+
+// The local posterior table (a multiple of 256 bytes); its class tables follow it.
+size_t table_bytes(const lead_code* code, int side) {
   const size_t b = (size_t)(1 << code->side[side].m_l) * code->nl * sizeof(float);
   return (b + 255) / 256 * 256;
 }
 
-namespace {
+}  // namespace
 
-size_t table_bytes(const lead_code* code, int side) { return decode_workspace_bytes(code, side); }
+size_t table_bytes_of(const lead_code* code, int side) { return table_bytes(code, side); }
+
+// The workspace lead_decode reads: the local posterior table and its class tables.
+size_t decode_workspace_bytes(const lead_code* code, int side) {
+  return table_bytes(code, side) + local_pair_extra_bytes(code, side);
+}
+
+namespace {
 
 int validate_opts(const lead_code* code, const lead_decode_opts* o) {
   if (!o || o->side < 0 || o->side > 1) return LEAD_EINVAL;
@@ -146,10 +149,8 @@ int launch_local(const lead_code* code, const lead_decode_opts* o, const uint32_
   a.syn = syn;
   a.table = table;
   a.qslots = code->dside[o->side].qslots;
-  a.llr_t0 = code->d_llr;
-  a.llr_t1 = code->d_llr + kLlrNodes;
   a.llr = llr;
-  const size_t smem = sizeof(uint32_t) * ((size_t)(1 << P.m_l) * NL + 1 + 2 * (size_t)kLlrNodes) +
+  const size_t smem = sizeof(uint32_t) * (size_t)(1 << P.m_l) * NL +
                       sizeof(uint16_t) * (size_t)kLocalShotBatch * code->order;
   const int kq = (code->n + kLocalThreads - 1) / kLocalThreads;
   auto pick = [&](auto kern) -> int {
@@ -174,10 +175,11 @@ int launch_local(const lead_code* code, const lead_decode_opts* o, const uint32_
 }  // namespace
 
 // The min-sum kernel (Phase 3) on one side. Its prior: per-qubit LLRs lam_in (shots x n) when
-// given, else the merged local posteriors of `table` (use_lead), else the channel LLR.
+// given, else the merged local posteriors of `table` (use_lead; with the class tables that follow
+// the table when `classes` is set), else the channel LLR.
 int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* syn, int64_t shots,
               uint32_t* corr, uint8_t* status, int32_t* iters, float* llr, const float* table,
-              cudaStream_t stream, const float* lam_in) {
+              cudaStream_t stream, const float* lam_in, void* classes) {
   BPJitArgs a{};
   a.n = code->n;
   a.words_n = code->words_n;
@@ -187,7 +189,7 @@ int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* 
   a.max_iter = o->max_iter;
   a.use_lead = o->use_lead ? 1 : 0;
   a.alpha = o->alpha;
-  a.p = o->p;
+  a.p = (float)o->p;
   a.shots = shots;
   a.syn = syn;
   a.corr = corr;
@@ -195,11 +197,15 @@ int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* 
   a.iters = iters;
   a.llr = llr;
   a.table = table;
+  if (table && classes) {
+    const ClassTables ct = class_tables(code, o->side, classes);
+    a.cls = ct.cls;
+    a.pair = reinterpret_cast<const float*>(ct.pair);
+    a.header = ct.header;
+  }
   a.lam = lam_in;
   a.pa = code->dside[o->side].bp_pa;
   a.views = code->dside[o->side].views;
-  a.llr_t0 = code->d_llr;
-  a.llr_t1 = code->d_llr + kLlrNodes;
   a.check = code->d_check;
   if (!a.pa) return LEAD_EINVAL;
   return jit_launch_bp(code, o->side, o->precision, a, sm_count(code->device), stream);
@@ -260,14 +266,18 @@ int lead_decode(const lead_code* code, const lead_decode_opts* opts, const uint3
   if (!syn || !corr || !status) return LEAD_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   float* table = nullptr;
+  void* classes = nullptr;
   if (opts->use_lead) {
-    if (!workspace || ((uintptr_t)workspace & 15) || ws_bytes < table_bytes(code, opts->side))
+    if (!workspace || ((uintptr_t)workspace & 15) || ws_bytes < decode_workspace_bytes(code, opts->side))
       return LEAD_EINVAL;
     table = static_cast<float*>(workspace);
+    classes = static_cast<char*>(workspace) + table_bytes(code, opts->side);
     rc = launch_table(code, opts->side, opts->p, table, s, opts->estimator, nullptr);
     if (rc != LEAD_OK) return rc;
+    rc = launch_classify(code, opts->side, opts->alpha, LEAD_PREC_FP32, table, classes, s);
+    if (rc != LEAD_OK) return rc;
   }
-  rc = launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s, nullptr);
+  rc = launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s, nullptr, classes);
   return rc == LEAD_OK ? check_result(code, stream) : rc;
 }
 
@@ -286,9 +296,10 @@ namespace lead {
 namespace {
 
 constexpr int kNoAllocMaxDevices = 64;
-static_assert(LEAD_NOALLOC_TABLE_BYTES % 256 == 0, "table scratch must be a whole number of 256-byte blocks");
+static_assert(LEAD_NOALLOC_TABLE_BYTES % 256 == 0, "scratch must be a whole number of 256-byte blocks");
 
-// Shared by every call on a device and kept until the process exits; holds the last call's table.
+// Shared by every call on a device and kept until the process exits; holds the last call's
+// local posterior table followed by its class tables.
 static __device__ __align__(256) float g_noalloc_table[LEAD_NOALLOC_TABLE_BYTES / sizeof(float)];
 
 std::mutex g_noalloc_mu;
@@ -320,19 +331,22 @@ extern "C" int lead_decode_noalloc(const lead_code* code, const lead_decode_opts
   rc = validate_opts(code, opts);
   if (rc != LEAD_OK) return rc;
   if (shots < 0) return LEAD_EINVAL;
-  if (opts->use_lead && table_bytes(code, opts->side) > (size_t)LEAD_NOALLOC_TABLE_BYTES) return LEAD_EINVAL;
+  if (shots == 0) return LEAD_OK;          // empty batch: nothing to read or write (as lead_decode)
+  if (!syn || !corr || !status) return LEAD_EINVAL;
+  if (opts->use_lead && decode_workspace_bytes(code, opts->side) > (size_t)LEAD_NOALLOC_TABLE_BYTES)
+    return LEAD_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
   float* table = nullptr;
+  void* classes = nullptr;
   if (opts->use_lead) {
     rc = noalloc_table(code->device, &table);
     if (rc != LEAD_OK) return rc;
-  }
-  if (shots == 0) return LEAD_OK;
-  if (!syn || !corr || !status) return LEAD_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
-  if (opts->use_lead) {
+    classes = reinterpret_cast<char*>(table) + table_bytes(code, opts->side);
     rc = launch_table(code, opts->side, opts->p, table, s, opts->estimator, nullptr);
     if (rc != LEAD_OK) return rc;
+    rc = launch_classify(code, opts->side, opts->alpha, LEAD_PREC_FP32, table, classes, s);
+    if (rc != LEAD_OK) return rc;
   }
-  rc = launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s, nullptr);
+  rc = launch_bp(code, opts, syn, shots, corr, status, iters, llr, table, s, nullptr, classes);
   return rc == LEAD_OK ? check_result(code, stream) : rc;
 }

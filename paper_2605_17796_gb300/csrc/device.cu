@@ -2,6 +2,7 @@
 // the per-p local posterior table (Phase 1 + boost).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -134,11 +135,10 @@ __global__ void fill_i32_kernel(int32_t* __restrict__ out, int n, int32_t value)
 // from 0; post_j = lambda + U_j; e_j = [post_j < 0]; iteration 0 tests the prior; stop at the
 // first t with H_v e = s, at most max_iter iterations). q_j = sigmoid(post_j), raised to 1/2 on
 // the bits of e when H_v e = s. iters[s] (nullable) = t | converged << 16.
-__global__ void minsum_table_kernel(SideParams P, int nl, double p, const float* __restrict__ t0,
-                                    const float* __restrict__ t1, int max_iter, float* __restrict__ table,
+__global__ void minsum_table_kernel(SideParams P, int nl, float p, int max_iter, float* __restrict__ table,
                                     int32_t* __restrict__ iters) {
   const int S = 1 << P.m_l;
-  const float lam = channel_llr(p, t0, t1);
+  const float lam = channel_llr(p);
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
     float post[kMaxDelta * kMaxDelta];
     float c2v[kMaxLocalRows][kMaxSupport];
@@ -200,17 +200,10 @@ __global__ void minsum_table_kernel(SideParams P, int nl, double p, const float*
   }
 }
 
-// Nodes and slopes of lambda(p) = ln((1 - p)/p) on [2^-23, 1/2] (see llr_interp), from the
-// binary64 logarithm series, rounded to binary32.
-__global__ void llr_table_kernel(float* __restrict__ t0, float* __restrict__ t1) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kLlrNodes; i += gridDim.x * blockDim.x) {
-    const double p0 = (double)__uint_as_float((unsigned)(i + kLlrNode0) << 16);
-    const double p1 = (double)__uint_as_float((unsigned)(i + 1 + kLlrNode0) << 16);
-    const double l0 = __dsub_rn(log_series_f64(__dsub_rn(1.0, p0)), log_series_f64(p0));
-    const double l1 = __dsub_rn(log_series_f64(__dsub_rn(1.0, p1)), log_series_f64(p1));
-    t0[i] = __double2float_rn(l0);
-    t1[i] = (i == kLlrNodes - 1) ? 0.0f : __double2float_rn(__ddiv_rn(__dsub_rn(l1, l0), __dsub_rn(p1, p0)));
-  }
+// lambda(p) of n probabilities (lead_prior_llr).
+__global__ void prior_llr_kernel(const float* __restrict__ p, float* __restrict__ llr, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    llr[i] = llr_f32(__ldg(p + i));
 }
 
 template <typename T>
@@ -344,17 +337,11 @@ int prepare_device(lead_code* code, int device) {
       return rc;
     }
   }
-  if (cudaMalloc(&code->d_llr, 2 * kLlrNodes * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&code->d_check, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+  if (cudaMalloc(&code->d_check, 5 * sizeof(unsigned long long)) != cudaSuccess) {
     release_device(code);
     return LEAD_EOOM;
   }
-  if (cudaMemset(code->d_check, 0, 4 * sizeof(unsigned long long)) != cudaSuccess) {
-    release_device(code);
-    return LEAD_ECUDA;
-  }
-  llr_table_kernel<<<(kLlrNodes + 255) / 256, 256>>>(code->d_llr, code->d_llr + kLlrNodes);
-  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+  if (cudaMemset(code->d_check, 0, 5 * sizeof(unsigned long long)) != cudaSuccess) {
     release_device(code);
     return LEAD_ECUDA;
   }
@@ -386,10 +373,8 @@ void release_device(lead_code* code) {
     cudaFree(ds.ckern);
     ds = DeviceSide{};
   }
-  cudaFree(code->d_llr);
   cudaFree(code->d_check);
   code->d_check = nullptr;
-  code->d_llr = nullptr;
   if (prev >= 0) cudaSetDevice(prev);
   code->device = -1;
 }
@@ -410,8 +395,8 @@ int launch_table(const lead_code* code, int side, double p, float* table, cudaSt
   if (estimator == LEAD_EST_MINSUM) {
     // the local code length Delta^2 bounds the iterations (the paper runs BP up to the length)
     const int S = 1 << hs.m_l;
-    minsum_table_kernel<<<(S + 127) / 128, 128, 0, stream>>>(hs.params, code->nl, p, code->d_llr,
-                                                              code->d_llr + kLlrNodes, code->nl, table, iters);
+    minsum_table_kernel<<<(S + 127) / 128, 128, 0, stream>>>(hs.params, code->nl, (float)p, code->nl, table,
+                                                              iters);
     LEAD_CUDA_TRY(cudaGetLastError());
     return LEAD_OK;
   }
@@ -458,6 +443,19 @@ int lead_code_check_record(const lead_code* code, uint64_t record[4]) {
   return LEAD_OK;
 }
 
+int lead_code_device_errors(const lead_code* code, uint32_t* flags, int32_t clear) {
+  if (!code || !flags) return LEAD_EINVAL;
+  if (code->device < 0) return LEAD_ESTATE;
+  int cur = -1;
+  LEAD_CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != code->device) return LEAD_ESTATE;
+  unsigned long long w = 0;
+  LEAD_CUDA_TRY(cudaMemcpy(&w, code->d_check + 4, sizeof(w), cudaMemcpyDeviceToHost));
+  *flags = (uint32_t)w;
+  if (clear) LEAD_CUDA_TRY(cudaMemset(code->d_check + 4, 0, sizeof(w)));
+  return LEAD_OK;
+}
+
 int lead_code_prepare(lead_code* code, int32_t device) {
   if (!code || device < 0) return LEAD_EINVAL;
   return lead::prepare_device(code, device);
@@ -473,6 +471,18 @@ int lead_code_get_enumerators(const lead_code* code, int32_t side, int32_t* N, i
   if (N) LEAD_CUDA_TRY(cudaMemcpy(N, ds.enumN, sz * sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (N1) LEAD_CUDA_TRY(cudaMemcpy(N1, ds.enumN1, sz * code->nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
   if (ml) LEAD_CUDA_TRY(cudaMemcpy(ml, ds.ml, (size_t)(1 << hs.m_l) * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  return LEAD_OK;
+}
+
+int lead_prior_llr(const float* p, float* llr, int64_t n, void* stream) {
+  if (n < 0) return LEAD_EINVAL;
+  if (n == 0) return LEAD_OK;
+  if (!p || !llr) return LEAD_EINVAL;
+  int dev = 0;
+  LEAD_CUDA_TRY(cudaGetDevice(&dev));
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)lead::sm_count(dev) * 8);
+  lead::prior_llr_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p, llr, n);
+  LEAD_CUDA_TRY(cudaGetLastError());
   return LEAD_OK;
 }
 

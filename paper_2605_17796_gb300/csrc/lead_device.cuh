@@ -59,6 +59,20 @@ __device__ __forceinline__ float sigmoid_f32(float post) {
 
 int sm_count(int device);
 
+// Class tables of a local posterior table, laid out in the `extra` workspace part that follows
+// the table (local_pair_extra_bytes): the class byte of every entry, header[0] = K (0 when the
+// table has more distinct values than a byte holds) and the K x K pair table.
+struct ClassTables {
+  uint8_t* cls;
+  int* header;
+  unsigned int* pair;
+};
+ClassTables class_tables(const lead_code* code, int side, void* extra);
+size_t local_pair_extra_bytes(const lead_code* code, int side);
+// Builds them on `stream` for alpha; pair entries in the storage format of `prec`.
+int launch_classify(const lead_code* code, int side, float alpha, int prec, const float* table, void* extra,
+                    cudaStream_t stream);
+
 // min(cap, remaining) for the shot loops of the persistent kernels.
 __host__ __device__ __forceinline__ int rows_left(int64_t cap, int64_t remaining) {
   return (int)(remaining < cap ? remaining : cap);

@@ -81,8 +81,8 @@ struct lead_code {
   lead::HostSide side[2];
   int32_t device = -1;
   lead::DeviceSide dside[2];
-  float* d_llr = nullptr;            // prior-LLR interpolation table: node values, then slopes
-  unsigned long long* d_check = nullptr;   // checked build: {failures, site, index, bound}
+  unsigned long long* d_check = nullptr;   // checked build: {failures, site, index, bound}; then the
+                                           // device error flags (lead_code_device_errors) in word 4
   mutable unsigned long long last_check[4] = {};   // the last record a call returned LEAD_ECHECK for
   std::mutex jit_mu;                 // guards the lazily compiled kernels of the 16-bit modes
 };

@@ -6,8 +6,7 @@
 // values its views see, lambda(alpha * ((q0 + q1) * 1/2)), so it is tabulated once per call over
 // the K x K pairs of distinct values, with the same binary32 arithmetic as the direct
 // evaluation (the results are bit-identical). Per (shot, qubit) the kernel then does two class
-// lookups and one pair lookup instead of two table lookups, the merge and the interpolated
-// logarithm.
+// lookups and one pair lookup instead of two table lookups, the merge and the logarithm.
 //
 //   classify_kernel   one CTA: the distinct values of the table (a hash set in shared memory),
 //                     ranked by value (class ids are deterministic), the class byte of every
@@ -62,8 +61,6 @@ struct ClassArgs {
   const float* table;     // T boosted local posteriors
   int T;
   float alpha;
-  const float* llr_t0;
-  const float* llr_t1;
   uint8_t* cls;           // T class ids
   int* header;            // [0] = K (0: more than kMaxClasses distinct values)
   unsigned int* pair;     // K x K stored LLR patterns (float bits or 16-bit patterns)
@@ -109,7 +106,7 @@ __global__ void __launch_bounds__(kClassThreads) classify_kernel(ClassArgs a) {
     a.cls[e] = (uint8_t)rank_of[find_or_insert(keys, __float_as_uint(__ldg(a.table + e)))];
   for (int idx = tid; idx < K * K; idx += blockDim.x) {
     const int c0 = idx / K, c1 = idx - c0 * K;
-    a.pair[idx] = llr_bits<PREC>(merged_llr(vals[c0], vals[c1], a.alpha, a.llr_t0, a.llr_t1));
+    a.pair[idx] = llr_bits<PREC>(merged_llr(vals[c0], vals[c1], a.alpha));
   }
   if (tid == 0) a.header[0] = K;
 }
@@ -126,8 +123,6 @@ struct PairArgs {
   const unsigned int* pair;
   const int* header;
   const float* table;           // direct evaluation when the pair table does not fit
-  const float* llr_t0;
-  const float* llr_t1;
   const uint32_t* qslots;
   void* llr;                    // float, or the 16-bit pattern of the storage format
   unsigned long long* check;    // checked build: bounds-failure record
@@ -170,7 +165,7 @@ __device__ __forceinline__ void batch_llrs(const PairArgs& a, const uint16_t* sv
             const int c0 = cls_s[e0], c1 = cls_s[e1];
             v = (in_bounds(a.check, c0, K, 11) && in_bounds(a.check, c1, K, 11)) ? pair_s[c0 * K + c1] : OutT(0);
           } else {
-            const float x = merged_llr(__ldg(a.table + e0), __ldg(a.table + e1), a.alpha, a.llr_t0, a.llr_t1);
+            const float x = merged_llr(__ldg(a.table + e0), __ldg(a.table + e1), a.alpha);
             if constexpr (PREC == LEAD_PREC_FP32) v = x;
             else v = (unsigned short)llr_bits<PREC>(x);
           }
@@ -230,20 +225,41 @@ size_t local_pair_extra_bytes(const lead_code* code, int side) {
 // Phases 1-2 through class and pair tables; `extra` (local_pair_extra_bytes, 16-byte aligned)
 // holds the class bytes, the header and the pair table. Returns LEAD_EINVAL for local codes
 // other than Delta = 4 or 6, or when the staged tables exceed one CTA's shared memory.
+ClassTables class_tables(const lead_code* code, int side, void* extra) {
+  const int T = (1 << code->side[side].params.m_l) * code->nl;
+  ClassTables t;
+  t.cls = static_cast<uint8_t*>(extra);
+  t.header = reinterpret_cast<int*>(t.cls + (T + 255) / 256 * 256);
+  t.pair = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(t.header) + 256);
+  return t;
+}
+
+// The class bytes, K and the K x K pair table of a local posterior table, for alpha, with the pair
+// entries stored in the format of `prec` (binary32 bits for LEAD_PREC_FP32).
+int launch_classify(const lead_code* code, int side, float alpha, int prec, const float* table, void* extra,
+                    cudaStream_t stream) {
+  const int T = (1 << code->side[side].params.m_l) * code->nl;
+  const ClassTables t = class_tables(code, side, extra);
+  ClassArgs c{table, T, alpha, t.cls, t.header, t.pair};
+  if (prec == LEAD_PREC_BF16) classify_kernel<LEAD_PREC_BF16><<<1, kClassThreads, 0, stream>>>(c);
+  else if (prec == LEAD_PREC_FP16) classify_kernel<LEAD_PREC_FP16><<<1, kClassThreads, 0, stream>>>(c);
+  else classify_kernel<LEAD_PREC_FP32><<<1, kClassThreads, 0, stream>>>(c);
+  LEAD_CUDA_TRY(cudaGetLastError());
+  return LEAD_OK;
+}
+
 int launch_local_pair(const lead_code* code, const lead_decode_opts* o, const uint32_t* syn, int64_t shots,
                       void* llr, const float* table, void* extra, cudaStream_t stream) {
   const SideParams& P = code->side[o->side].params;
   const int nl = code->nl;
   if (nl != 16 && nl != 36) return LEAD_EINVAL;
   const int T = (1 << P.m_l) * nl;
-  uint8_t* cls = static_cast<uint8_t*>(extra);
-  int* header = reinterpret_cast<int*>(cls + (T + 255) / 256 * 256);
-  unsigned int* pair = reinterpret_cast<unsigned int*>(reinterpret_cast<char*>(header) + 256);
-  ClassArgs c{table, T, o->alpha, code->d_llr, code->d_llr + kLlrNodes, cls, header, pair};
-  if (o->precision == LEAD_PREC_BF16) classify_kernel<LEAD_PREC_BF16><<<1, kClassThreads, 0, stream>>>(c);
-  else if (o->precision == LEAD_PREC_FP16) classify_kernel<LEAD_PREC_FP16><<<1, kClassThreads, 0, stream>>>(c);
-  else classify_kernel<LEAD_PREC_FP32><<<1, kClassThreads, 0, stream>>>(c);
-  LEAD_CUDA_TRY(cudaGetLastError());
+  const ClassTables ct = class_tables(code, o->side, extra);
+  uint8_t* cls = ct.cls;
+  int* header = ct.header;
+  unsigned int* pair = ct.pair;
+  int rc = launch_classify(code, o->side, o->alpha, o->precision, table, extra, stream);
+  if (rc != LEAD_OK) return rc;
 
   PairArgs a{};
   a.n = code->n;
@@ -258,8 +274,6 @@ int launch_local_pair(const lead_code* code, const lead_decode_opts* o, const ui
   a.pair = pair;
   a.header = header;
   a.table = table;
-  a.llr_t0 = code->d_llr;
-  a.llr_t1 = code->d_llr + kLlrNodes;
   a.qslots = code->dside[o->side].qslots;
   a.llr = llr;
   a.check = code->d_check;

@@ -149,8 +149,7 @@ __host__ __device__ inline OsdLayout osd_layout(int n, int m, bool big) {
 // the shared-memory variant the compiler sees shared-memory addresses. WIDE: rows of more than
 // 64 words, applied in 64-word chunks.
 template <bool BIG, bool WIDE>
-__global__ void __launch_bounds__(kOsdThreads, 2) osd_kernel(OsdArgs a, double p_ch, const float* __restrict__ t0,
-                                                          const float* __restrict__ t1,
+__global__ void __launch_bounds__(kOsdThreads, 2) osd_kernel(OsdArgs a, float p_ch,
                                                           __grid_constant__ const SideParams P) {
   extern __shared__ __align__(16) unsigned char sm[];
   const OsdLayout L = osd_layout(a.n, a.m, BIG);
@@ -178,7 +177,7 @@ __global__ void __launch_bounds__(kOsdThreads, 2) osd_kernel(OsdArgs a, double p
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = bd >> 5;
   const int n = a.n, m = a.m, W = a.w64;
   const int nw32 = (n + 31) / 32;
-  const float lam_ch = channel_llr(p_ch, t0, t1);
+  const float lam_ch = channel_llr(p_ch);
 
   for (int64_t shot = blockIdx.x; shot < a.shots; shot += gridDim.x) {
     if (a.status[shot] & LEAD_ST_CONVERGED) continue;      // uniform across the CTA
@@ -502,8 +501,7 @@ int lead_osd(const lead_code* code, const lead_decode_opts* opts, int32_t order,
   a.garr_bytes = L.big ? L.gmem : 0;
   a.garr = static_cast<unsigned char*>(workspace) + (size_t)slots * mat_bytes;
   a.check = code->d_check;
-  kern<<<slots, kOsdThreads, L.smem, (cudaStream_t)stream>>>(a, opts->p > 0.0 ? opts->p : 0.25, code->d_llr,
-                                                                     code->d_llr + kLlrNodes, hs.params);
+  kern<<<slots, kOsdThreads, L.smem, (cudaStream_t)stream>>>(a, (float)(opts->p > 0.0 ? opts->p : 0.25), hs.params);
   LEAD_CUDA_TRY(cudaGetLastError());
   return check_result(code, stream);
 }

@@ -14,17 +14,29 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "bp_jit_args.h"
 #include "lead_device.cuh"
 
 namespace lead {
 int check_device(const lead_code* code);
+int run_prior_local_tc(const lead_code* code, int side, const uint32_t* syn, int64_t shots, const float* lam,
+                       float* Q, uint64_t* ml, unsigned int* err, cudaStream_t stream);
 int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* syn, int64_t shots,
               uint32_t* corr, uint8_t* status, int32_t* iters, float* llr, const float* table,
-              cudaStream_t stream, const float* lam_in);
+              cudaStream_t stream, const float* lam_in, void* classes);
 
 namespace {
+
+// The local posterior under per-qubit priors runs on the tensor cores (prior_tc.cu). Setting
+// LEAD_PRIOR_SIMT=1 in the environment (read at every call) selects the CUDA-core kernel below
+// instead (the same reading of Phase 1, one warp per item, both contractions as gathers), so the
+// two can be compared on the same inputs.
+bool prior_simt() {
+  const char* e = std::getenv("LEAD_PRIOR_SIMT");
+  return e && e[0] && e[0] != '0';
+}
 
 constexpr int kPriorWarps = 8;
 
@@ -37,8 +49,6 @@ struct PriorArgs {
   const uint8_t* xcls;        // 2^Delta row patterns, class-major, increasing within a class
   const uint32_t* cbase;      // 2^m_l packed row images
   const uint32_t* ckern;      // NK packed kernel elements
-  const float* t0;
-  const float* t1;
   float* Q;                   // items x nl boosted local posteriors
   unsigned long long* ml;     // items: least-cost local decision (bit j = local index j), or null
 };
@@ -66,7 +76,7 @@ __global__ void __launch_bounds__(kPriorWarps * 32) prior_local_kernel(PriorArgs
     // A: prior LLRs and integer costs of the view's positions, stored as [row a][column b]
     for (int j = lane; j < NL; j += 32) {
       const int q = __ldg(a.views + v * NL + j);
-      const float w = llr_interp(__ldg(a.prior + shot * a.n + q), a.t0, a.t1);
+      const float w = llr_f32(__ldg(a.prior + shot * a.n + q));
       const int ia = j % DELTA, ib = j / DELTA;
       s_w[wid][ia][ib] = w;
       s_W[wid][ia][ib] = __float2int_rn(__fmul_rn(w, 1048576.0f));
@@ -223,8 +233,6 @@ struct MergeArgs {
   float alpha;
   const float* Q;
   const uint32_t* qslots;
-  const float* t0;
-  const float* t1;
   float* llr;
 };
 
@@ -237,16 +245,15 @@ __global__ void prior_merge_kernel(MergeArgs a) {
     const int i = (int)(idx - shot * a.n);
     const uint32_t s0 = __ldg(a.qslots + 2 * i), s1 = __ldg(a.qslots + 2 * i + 1);
     const float* Qs = a.Q + shot * (int64_t)a.order * a.nl;
-    a.llr[idx] = merged_llr(Qs[s0], Qs[s1], a.alpha, a.t0, a.t1);
+    a.llr[idx] = merged_llr(Qs[s0], Qs[s1], a.alpha);
   }
 }
 
 // The standalone baseline with per-qubit priors: lambda(p_i) for every qubit.
-__global__ void prior_channel_kernel(int64_t total, const float* prior, const float* t0, const float* t1,
-                                     float* llr) {
+__global__ void prior_channel_kernel(int64_t total, const float* prior, float* llr) {
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x)
-    llr[idx] = llr_interp(__ldg(prior + idx), t0, t1);
+    llr[idx] = llr_f32(__ldg(prior + idx));
 }
 
 template <int DELTA, int KB, int ML, int NK>
@@ -264,8 +271,6 @@ int launch_prior_local(const lead_code* code, int side, const uint32_t* syn, int
   a.xcls = ds.xcls;
   a.cbase = ds.cbase;
   a.ckern = ds.ckern;
-  a.t0 = code->d_llr;
-  a.t1 = code->d_llr + kLlrNodes;
   a.Q = Q;
   a.ml = reinterpret_cast<unsigned long long*>(ml);
   const int64_t blocks = std::min<int64_t>((a.items + kPriorWarps - 1) / kPriorWarps,
@@ -292,15 +297,16 @@ int run_prior_local(const lead_code* code, int side, const uint32_t* syn, int64_
 
 int run_prior_llr(const lead_code* code, const lead_decode_opts* o, const uint32_t* syn, int64_t shots,
                   const float* prior, float* llr, float* Q, uint64_t* ml, cudaStream_t stream) {
-  if (!o->use_lead) {
-    const int64_t total = shots * code->n;
-    const int64_t blocks = std::min<int64_t>((total + 255) / 256, (int64_t)sm_count(code->device) * 8);
-    prior_channel_kernel<<<(unsigned)blocks, 256, 0, stream>>>(total, prior, code->d_llr, code->d_llr + kLlrNodes,
-                                                                llr);
-    LEAD_CUDA_TRY(cudaGetLastError());
-    return LEAD_OK;
-  }
-  int rc = run_prior_local(code, o->side, syn, shots, prior, Q, ml, stream);
+  // lambda(p_i) for every qubit: the baseline's prior, and with the local stage the input of the
+  // local posterior kernel (the merge below then overwrites it with the merged LLRs)
+  const int64_t total = shots * code->n;
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, (int64_t)sm_count(code->device) * 8);
+  prior_channel_kernel<<<(unsigned)blocks, 256, 0, stream>>>(total, prior, llr);
+  LEAD_CUDA_TRY(cudaGetLastError());
+  if (!o->use_lead) return LEAD_OK;
+  int rc = prior_simt() ? run_prior_local(code, o->side, syn, shots, prior, Q, ml, stream)
+                        : run_prior_local_tc(code, o->side, syn, shots, llr, Q, ml,
+                                             reinterpret_cast<unsigned int*>(code->d_check + 4), stream);
   if (rc != LEAD_OK) return rc;
   MergeArgs m{};
   m.n = code->n;
@@ -310,11 +316,7 @@ int run_prior_llr(const lead_code* code, const lead_decode_opts* o, const uint32
   m.alpha = o->alpha;
   m.Q = Q;
   m.qslots = code->dside[o->side].qslots;
-  m.t0 = code->d_llr;
-  m.t1 = code->d_llr + kLlrNodes;
   m.llr = llr;
-  const int64_t total = shots * code->n;
-  const int64_t blocks = std::min<int64_t>((total + 255) / 256, (int64_t)sm_count(code->device) * 8);
   prior_merge_kernel<<<(unsigned)blocks, 256, 0, stream>>>(m);
   LEAD_CUDA_TRY(cudaGetLastError());
   return LEAD_OK;
@@ -420,7 +422,7 @@ int lead_decode_priors(const lead_code* code, const lead_decode_opts* opts, cons
     rc = run_prior_llr(code, opts, syn + c0 * wm, cn, prior + c0 * n, lam, Q, nullptr, s);
     if (rc != LEAD_OK) return rc;
     rc = launch_bp(code, opts, syn + c0 * wm, cn, corr + c0 * wn, status + c0, iters ? iters + c0 : nullptr,
-                   llr ? llr + c0 * n : nullptr, nullptr, s, lam);
+                   llr ? llr + c0 * n : nullptr, nullptr, s, lam, nullptr);
     if (rc != LEAD_OK) return rc;
   }
   return check_result(code, stream);

@@ -8,7 +8,9 @@
 // budget. Completion is detected with cudaEventQuery (no host or device spin on the GPU);
 // results carry the request id, per-side status, the correction and the latency from arrival to
 // completion. Each shot's decode is independent of the others in its batch, so a request's
-// result does not depend on what it was batched with.
+// result does not depend on what it was batched with. The per-(code, side) tables of Phases 1-2
+// (the local posterior table for the code's p and its class tables) are built once when the
+// server is created and shared by every batch, so a batch launches only the min-sum kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +24,17 @@
 #include <vector>
 
 #include "lead_internal.h"
+
+namespace lead {
+int launch_table(const lead_code* code, int side, double p, float* table, cudaStream_t stream, int estimator,
+                 int32_t* iters);
+int launch_classify(const lead_code* code, int side, float alpha, int prec, const float* table, void* extra,
+                    cudaStream_t stream);
+int launch_bp(const lead_code* code, const lead_decode_opts* o, const uint32_t* syn, int64_t shots,
+              uint32_t* corr, uint8_t* status, int32_t* iters, float* llr, const float* table,
+              cudaStream_t stream, const float* lam_in, void* classes);
+size_t table_bytes_of(const lead_code* code, int side);
+}  // namespace lead
 
 namespace {
 
@@ -44,7 +57,6 @@ struct Slot {
   uint32_t* d_syn = nullptr;     // max_batch x (wm0 + wm1)
   uint32_t* d_corr = nullptr;    // 2 x max_batch x words_n
   uint8_t* d_status = nullptr;   // 2 x max_batch
-  void* d_ws = nullptr;          // local table workspace (one per side)
   uint32_t* h_syn = nullptr;     // pinned staging
   uint32_t* h_corr = nullptr;
   uint8_t* h_status = nullptr;
@@ -61,7 +73,7 @@ struct lead_server {
   int32_t sides_mask = 3, max_batch = 0, max_iter = 32;
   float alpha = 1.0f;
   int32_t wm[2] = {0, 0}, wn = 0;    // maxima over the codes
-  size_t ws_bytes = 0;
+  std::vector<void*> tables;          // per code, per side: local posterior table + class tables
   int device = 0;
   std::vector<Slot> slots;
   Clock::time_point t0;
@@ -103,9 +115,11 @@ int launch_batch(lead_server* s, Slot& sl) {
     o.precision = LEAD_PREC_FP32;
     o.alpha = s->alpha;
     o.p = s->p_side[sl.code];
-    int rc = lead_decode(code, &o, d_side[side], n, sl.d_corr + (size_t)side * s->max_batch * s->wn,
-                         sl.d_status + (size_t)side * s->max_batch, nullptr, nullptr,
-                         static_cast<char*>(sl.d_ws) + side * s->ws_bytes, s->ws_bytes, sl.stream);
+    char* tab = static_cast<char*>(s->tables[2 * (size_t)sl.code + side]);
+    int rc = lead::launch_bp(code, &o, d_side[side], n, sl.d_corr + (size_t)side * s->max_batch * s->wn,
+                             sl.d_status + (size_t)side * s->max_batch, nullptr, nullptr,
+                             reinterpret_cast<const float*>(tab), sl.stream, nullptr,
+                             tab + lead::table_bytes_of(code, side));
     if (rc != LEAD_OK) return rc;
   }
   for (int side = 0; side < 2; ++side) {
@@ -206,12 +220,39 @@ void free_slots(lead_server* s) {
     cudaFree(sl.d_syn);
     cudaFree(sl.d_corr);
     cudaFree(sl.d_status);
-    cudaFree(sl.d_ws);
     cudaFreeHost(sl.h_syn);
     cudaFreeHost(sl.h_corr);
     cudaFreeHost(sl.h_status);
   }
   s->slots.clear();
+  for (void* t : s->tables) cudaFree(t);
+  s->tables.clear();
+}
+
+// The Phases 1-2 tables of every (code, side) the server decodes, built once on the device.
+int build_tables(lead_server* s) {
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return LEAD_ECUDA;
+  int rc = LEAD_OK;
+  s->tables.assign(2 * s->codes.size(), nullptr);
+  for (size_t c = 0; c < s->codes.size() && rc == LEAD_OK; ++c) {
+    const lead_code* code = s->codes[c];
+    for (int side = 0; side < 2 && rc == LEAD_OK; ++side) {
+      if (!((s->sides_mask >> side) & 1)) continue;
+      void*& t = s->tables[2 * c + side];
+      if (cudaMalloc(&t, lead::decode_workspace_bytes(code, side)) != cudaSuccess) {
+        rc = LEAD_EOOM;
+        break;
+      }
+      rc = lead::launch_table(code, side, s->p_side[c], static_cast<float*>(t), st, LEAD_EST_EXACT, nullptr);
+      if (rc == LEAD_OK)
+        rc = lead::launch_classify(code, side, s->alpha, LEAD_PREC_FP32, static_cast<float*>(t),
+                                   static_cast<char*>(t) + lead::table_bytes_of(code, side), st);
+    }
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == LEAD_OK) rc = LEAD_ECUDA;
+  cudaStreamDestroy(st);
+  return rc;
 }
 
 }  // namespace
@@ -239,18 +280,13 @@ int lead_server_create(const lead_server_config* cfg, lead_server** out) {
     s->device = code->device;
     s->codes.push_back(code);
     s->p_side.push_back(cfg->p_side[c]);
-    for (int side = 0; side < 2; ++side) {
-      s->wm[side] = std::max(s->wm[side], code->side[side].params.words_m);
-      // the server only decodes: the local table, not lead_local_estimate's class tables
-      s->ws_bytes = std::max(s->ws_bytes, lead::decode_workspace_bytes(code, side));
-    }
+    for (int side = 0; side < 2; ++side) s->wm[side] = std::max(s->wm[side], code->side[side].params.words_m);
     s->wn = std::max(s->wn, code->words_n);
   }
   s->ready.resize(cfg->ncodes);
   // memory admission: as many slots as the budget allows, at most cfg->streams
   const size_t per_slot = sizeof(uint32_t) * (size_t)s->max_batch * (s->wm[0] + s->wm[1]) +
-                          sizeof(uint32_t) * 2 * (size_t)s->max_batch * s->wn + 2 * (size_t)s->max_batch +
-                          2 * s->ws_bytes + 1024;
+                          sizeof(uint32_t) * 2 * (size_t)s->max_batch * s->wn + 2 * (size_t)s->max_batch + 1024;
   const int nslots = (int)std::min<size_t>((size_t)cfg->streams, cfg->budget_bytes / per_slot);
   if (nslots < 1) {
     delete s;
@@ -269,7 +305,6 @@ int lead_server_create(const lead_server_config* cfg, lead_server** out) {
         cudaMalloc(&sl.d_syn, sizeof(uint32_t) * wsyn) != cudaSuccess ||
         cudaMalloc(&sl.d_corr, sizeof(uint32_t) * wcor) != cudaSuccess ||
         cudaMalloc(&sl.d_status, 2 * (size_t)s->max_batch) != cudaSuccess ||
-        cudaMalloc(&sl.d_ws, 2 * s->ws_bytes + 256) != cudaSuccess ||
         cudaMallocHost(&sl.h_syn, sizeof(uint32_t) * wsyn) != cudaSuccess ||
         cudaMallocHost(&sl.h_corr, sizeof(uint32_t) * wcor) != cudaSuccess ||
         cudaMallocHost(&sl.h_status, 2 * (size_t)s->max_batch) != cudaSuccess) {
@@ -277,6 +312,12 @@ int lead_server_create(const lead_server_config* cfg, lead_server** out) {
       delete s;
       return LEAD_EOOM;
     }
+  }
+  const int trc = build_tables(s);
+  if (trc != LEAD_OK) {
+    free_slots(s);
+    delete s;
+    return trc;
   }
   s->t0 = Clock::now();
   s->worker = std::thread(run, s);

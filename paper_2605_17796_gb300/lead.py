@@ -24,6 +24,7 @@ ECHECK = -10                      # checked build: a kernel index failed its bou
 BUILD_CHECKED = 1                 # lead_build_flags() bit of the checked build
 PREC_FP32, PREC_BF16, PREC_FP16 = 0, 1, 2
 EST_EXACT, EST_MINSUM = 0, 1
+NOALLOC_TABLE_BYTES = 444928      # LEAD_NOALLOC_TABLE_BYTES: the fixed tables of lead_decode_noalloc
 
 _c_int32_p = ctypes.POINTER(ctypes.c_int32)
 _c_uint8_p = ctypes.POINTER(ctypes.c_uint8)
@@ -74,6 +75,7 @@ EXPORTS = {
     "lead_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_int64,
                                    ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "lead_prior_llr": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "lead_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.POINTER(LeadDecodeOpts), ctypes.c_int64]),
     "lead_local_table": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p,
                                         ctypes.c_void_p]),
@@ -113,6 +115,7 @@ EXPORTS = {
     "lead_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lead_build_flags": (ctypes.c_int, []),
     "lead_code_check_record": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "lead_code_device_errors": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32]),
     "lead_server_create": (ctypes.c_int, [ctypes.POINTER(LeadServerConfig), ctypes.POINTER(ctypes.c_void_p)]),
     "lead_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]),
@@ -164,6 +167,14 @@ def _stream(stream=None) -> int | None:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return s.cuda_stream
+
+
+def prior_llr(p, llr, stream=None):
+    """llr[i] = lambda(p[i]) = ln((1 - p[i])/p[i]) in binary32 (lead_prior_llr); p, llr float32 CUDA
+    tensors of the same size."""
+    if p.numel() != llr.numel():
+        raise ValueError("p and llr must have the same number of elements")
+    _check("lead_prior_llr", LIB.lead_prior_llr(_ptr(p), _ptr(llr), p.numel(), _stream(stream)))
 
 
 @dataclass
@@ -346,6 +357,12 @@ class Code:
         rec = (ctypes.c_uint64 * 4)()
         _check("lead_code_check_record", LIB.lead_code_check_record(self._h, rec))
         return tuple(int(x) for x in rec)
+
+    def device_errors(self, clear: bool = False) -> int:
+        """Device error flags of the code's kernels (lead_code_device_errors; waits for the device)."""
+        f = ctypes.c_uint32()
+        _check("lead_code_device_errors", LIB.lead_code_device_errors(self._h, ctypes.byref(f), 1 if clear else 0))
+        return int(f.value)
 
     def check(self, side: int, err, corr, shots: int, fail, stream=None):
         _check("lead_check", LIB.lead_check(self._h, side, _ptr(err), _ptr(corr), shots, _ptr(fail),

@@ -1,18 +1,21 @@
 """Per-qubit priors (lead_local_estimate_priors / lead_decode_priors) against the oracle.
 
 Bar:
-* least-cost local decisions (integer costs, exact sums): bit-exact;
+* least-cost local decisions (integer costs W_j = rint(2^20 lambda(p_j)), exact sums): bit-exact;
 * boosted local posteriors: relative error <= 1e-4 against the oracle's FP64 posterior of the
-  priors the kernel sees, p' = 1/(1 + e^lambda_f32(p)). The kernel sums at most 36 binary32
-  prior LLRs (|lambda| < 16) per log-weight and 6 log-sums per coset member, which keeps every
-  exponent within ~6e-5 of its exact value for the priors drawn here (p <= 0.15, |lambda| < 7):
-  a relative error below 1e-4 of every term, and of the ratios q = num / Z;
-* against the FP64 posterior of the exact priors p, relative error <= 1e-3: the interpolated
-  lambda_f32 differs from ln((1-p)/p) by at most 1e-5, 36 of them per term and two terms in a
-  ratio bound the log-error by 7.2e-4;
+  exact priors. The kernel takes lambda(p) rounded to binary32 (relative error 2^-24), sums at
+  most 6 of them per row pattern and 6 row log-sums per coset member in binary32, and evaluates
+  the log-sum-exps in binary32: every exponent is within about 1e-5 of its exact value, so every
+  term and every ratio q = num / Z stays within about 2e-5;
 * merged prior LLRs: bit-exact with the oracle's binary32 merge applied to the kernel's own
   posteriors;
-* global min-sum with those LLRs: corrections, status, iterations and posteriors bit-exact.
+* the whole decode from the raw priors and syndromes: the oracle runs its own FP64 local
+  posteriors, the binary32 merge and min-sum. A posterior that differs from the kernel's in its
+  last bits can move a merged LLR by an ulp and change a min-sum trajectory (most visibly in
+  shots that do not converge, whose last decision wanders), so two counts are held under stated
+  bounds: shots whose decoder-failure verdict differs, and shots converged on both sides with
+  different corrections; the count of shots with any difference is printed. With use_lead = 0
+  (the prior LLR alone) the decode is bit-exact.
 """
 import numpy as np
 import pytest
@@ -69,12 +72,6 @@ def _estimate(L, code, side, syn, prior, alpha=1.0, with_q=True):
             ml.cpu().numpy().view(np.uint64).astype(np.int64))
 
 
-def _effective(prior):
-    """The priors whose exact LLRs are the kernel's binary32 lambda_f32(p)."""
-    lam = olocal.llr_f32(prior).astype(np.float64)
-    return 1.0 / (1.0 + np.exp(lam))
-
-
 @pytest.mark.parametrize("name,side,p,shots", [("SL(2,3)", 0, 0.05, 9), ("SL(2,3)", 1, 0.1, 7),
                                                ("PSL(2,7)", 0, 0.03, 2), ("PSL(2,7)", 1, 0.06, 2)])
 def test_local_priors_parity(codes, L, name, side, p, shots):
@@ -83,11 +80,9 @@ def test_local_priors_parity(codes, L, name, side, p, shots):
     llr, q, ml = _estimate(L, code, side, syn, prior)
     want_q, want_ml = olead.local_priors(oc, side, syn, prior)
     assert (ml == want_ml).all()
-    eff_q, _ = olead.local_priors(oc, side, syn, _effective(prior), boost=False)
-    flip = ((want_ml[..., None] >> np.arange(inst.delta ** 2)) & 1).astype(bool)
-    eff_q = np.where(flip, np.maximum(eff_q, 0.5), eff_q)            # boost on the pinned decision
-    assert np.all(np.abs(q - eff_q) <= 1e-4 * eff_q + 1e-30)
-    assert np.all(np.abs(q - want_q) <= 1e-3 * want_q + 1e-30)
+    rel = np.abs(q - want_q) / np.maximum(want_q, 1e-30)
+    print(f"{name} side {side}: max relative error of q against FP64 {rel.max():.2e}")
+    assert np.all(np.abs(q - want_q) <= 1e-4 * want_q + 1e-30)
     # every least-cost decision satisfies its local syndrome
     Hl = np.kron(oc.sides[side].RB, oc.sides[side].RA).astype(np.int64)
     sv = olead.local_syndromes(oc.sides[side], syn)
@@ -112,7 +107,7 @@ def test_uniform_priors_reduce_to_table_path(codes, L, name):
         assert (ml == oml[sv]).all()                                  # least cost = least weight
         table = olocal.boosted_table_f32(N, N1, oml, p).astype(np.float64)
         want = table[sv]
-        assert np.all(np.abs(q - want) <= 1e-3 * want + 1e-30)
+        assert np.all(np.abs(q - want) <= 1e-4 * want + 1e-30)
 
 
 def _decode_priors(L, code, side, syn, prior, use_lead=True, alpha=1.0, max_iter=32):
@@ -131,25 +126,53 @@ def _decode_priors(L, code, side, syn, prior, use_lead=True, alpha=1.0, max_iter
             it.cpu().numpy(), post.cpu().numpy())
 
 
+# fractions of the decoded shots allowed a different failure verdict, and a different correction
+# among the shots converged on both sides, against the oracle run from raw inputs
+VERDICT_BOUND = 0.05
+CONVERGED_BOUND = 0.05
+
+
 @pytest.mark.parametrize("name,side,p,shots,use_lead", [
-    ("SL(2,3)", 0, 0.05, 40, True), ("SL(2,3)", 1, 0.08, 30, False),
-    ("PSL(2,7)", 0, 0.02, 12, True), ("PSL(2,7)", 1, 0.03, 12, True), ("PSL(2,7)", 0, 0.03, 10, False),
+    ("SL(2,3)", 0, 0.05, 200, True), ("SL(2,3)", 1, 0.08, 60, False),
+    ("PSL(2,7)", 0, 0.02, 40, True), ("PSL(2,7)", 1, 0.03, 40, True), ("PSL(2,7)", 0, 0.03, 20, False),
     ("PSL(2,11)", 0, 0.02, 3, True), ("PSL(2,11)", 1, 0.02, 3, False)])
-def test_decode_priors_bit_exact(codes, L, name, side, p, shots, use_lead):
+def test_decode_priors_from_raw_inputs(codes, L, name, side, p, shots, use_lead):
     inst, code, oc = codes[name]
     prior, e, syn = _inputs(oc, side, shots, p, seed=13)
     corr, st, it, post = _decode_priors(L, code, side, syn, prior, use_lead=use_lead)
     if use_lead:
-        lam, _, _ = _estimate(L, code, side, syn, prior, with_q=False)
+        q, _ = olead.local_priors(oc, side, syn, prior)
+        lam = olead.merge_priors_f32(oc, side, q)
     else:
         lam = olocal.llr_f32(prior)
     H = oc.sides[side].H
     wc, wst, wit, wpost = olead.min_sum(H, oc.sides[side].m_l, syn, lam, 32)
-    assert (st == wst).all() and (it == wit).all()
-    assert (corr == wc).all()
-    assert (post.view(np.uint32) == wpost.view(np.uint32)).all()
     conv = st == L.ST_CONVERGED
-    assert (philox.syndromes(H, wc)[conv] == syn[conv]).all()
+    assert (philox.syndromes(H, corr)[conv] == syn[conv]).all()
+    if not use_lead:
+        assert (st == wst).all() and (it == wit).all() and (corr == wc).all()
+        assert (post.view(np.uint32) == wpost.view(np.uint32)).all()
+        return
+    bad = (st != wst) | (it != wit) | (corr != wc).any(axis=1)
+    verdict = int((st != wst).sum())
+    both = (st == L.ST_CONVERGED) & (wst == L.ST_CONVERGED)
+    conv_diff = int(((corr != wc).any(axis=1) & both).sum())
+    print(f"{name} side {side} p={p}: {int(bad.sum())}/{shots} shots differ from the oracle run from raw "
+          f"inputs; failure verdicts differ on {verdict}; converged on both {int(both.sum())}, of them with "
+          f"different corrections {conv_diff}")
+    assert verdict <= max(1, int(VERDICT_BOUND * shots))
+    assert conv_diff <= max(1, int(CONVERGED_BOUND * shots))
+
+
+def test_decode_priors_bit_exact_on_its_own_llrs(codes, L):
+    """Phase 3 alone: min-sum from the kernel's own merged LLRs equals the oracle's, bit for bit."""
+    inst, code, oc = codes["PSL(2,7)"]
+    prior, e, syn = _inputs(oc, 0, 12, 0.02, seed=13)
+    corr, st, it, post = _decode_priors(L, code, 0, syn, prior)
+    lam, _, _ = _estimate(L, code, 0, syn, prior, with_q=False)
+    wc, wst, wit, wpost = olead.min_sum(oc.sides[0].H, oc.sides[0].m_l, syn, lam, 32)
+    assert (st == wst).all() and (it == wit).all() and (corr == wc).all()
+    assert (post.view(np.uint32) == wpost.view(np.uint32)).all()
 
 
 def test_passes_split_large_batches(codes, L):
@@ -172,7 +195,7 @@ def test_passes_split_large_batches(codes, L):
     assert (post[rows].view(np.uint32) == post_r.view(np.uint32)).all()
     want_q, want_ml = olead.local_priors(oc, side, syn[rows[[2, 3]]], prior[rows[[2, 3]]])
     assert (ml_r[[2, 3]] == want_ml).all()
-    assert np.all(np.abs(q_r[[2, 3]] - want_q) <= 1e-3 * want_q + 1e-30)
+    assert np.all(np.abs(q_r[[2, 3]] - want_q) <= 1e-4 * want_q + 1e-30)
 
 
 def test_priors_edges(codes, L):

@@ -1,11 +1,16 @@
-"""The continuous-batching decode server: every result equals the batch decode of the same shot,
-whether the request was served alone or mixed with other codes' traffic; memory admission."""
+"""The continuous-batching decode server over SL(2,3), PSL(2,7) and PSL(2,11) (the serving
+workload mixes the last two): every result equals the batch decode of the same shot, whether the
+request was served alone or mixed with other codes' traffic; sampled results of each code equal
+the oracle's decode of the same shot (both sides); memory admission."""
 import numpy as np
 import pytest
 
 import workloads
 
 pytestmark = pytest.mark.gpu
+
+NAMES = ("SL(2,3)", "PSL(2,7)", "PSL(2,11)")
+ROWS = (100, 150, 60)
 
 torch = pytest.importorskip("torch")
 
@@ -15,9 +20,9 @@ def setup():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
     from paper_2605_17796_gb300 import lead, serving
-    codes = [lead.Code.from_instance(workloads.standard(n, 0)).prepare(0) for n in ("SL(2,3)", "PSL(2,7)")]
+    codes = [lead.Code.from_instance(workloads.standard(n, 0)).prepare(0) for n in NAMES]
     p = 0.03
-    rows = [serving.request_rows(c, p, 150, seed=21 + i) for i, c in enumerate(codes)]
+    rows = [serving.request_rows(c, p, k, seed=21 + i) for i, (c, k) in enumerate(zip(codes, ROWS))]
     # reference: one batch decode per code and side, with the same options as the server
     ref = []
     for c, r in zip(codes, rows):
@@ -51,26 +56,41 @@ def _check(res, cor, codes, ref, key_of):
 
 def test_mixed_traffic_matches_batch_decode(setup):
     lead, serving, codes, rows, ref, p = setup
-    srv = lead.Server(codes, [2 * p / 3] * 2, max_batch=32, streams=3, budget_bytes=256 << 20)
+    srv = lead.Server(codes, [2 * p / 3] * 3, max_batch=32, streams=3, budget_bytes=256 << 20)
     rng = np.random.default_rng(0)
     n = sum(r.shape[0] for r in rows)
-    arrival, code_of = serving.poisson_trace(2e5, n, [0.5, 0.5], rng)
-    # use every row of both codes exactly once
-    code_of = np.array([0] * rows[0].shape[0] + [1] * rows[1].shape[0], dtype=np.int32)[rng.permutation(n)]
+    arrival, code_of = serving.poisson_trace(2e5, n, [1, 1, 1], rng)
+    # use every row of every code exactly once
+    code_of = np.concatenate([[c] * r.shape[0] for c, r in enumerate(rows)]).astype(np.int32)[rng.permutation(n)]
     res, cor = serving.run_trace(srv, rows, arrival, code_of)
     idx = np.zeros(n, dtype=np.int64)
-    for c in (0, 1):
+    for c in range(len(codes)):
         sel = np.nonzero(code_of == c)[0]
         idx[sel] = np.arange(sel.size)
     _check(res, cor, codes, ref, lambda rid: (int(code_of[rid]), int(idx[rid])))
     assert srv.pending() == 0
     srv.close()
+    # sampled requests of each code against the oracle (the server decoded row i of code c from
+    # the depolarizing shot i of seed 21 + c)
+    from oracle import lead as olead, philox, tanner
+    for c, name in enumerate(NAMES):
+        oc = tanner.from_instance(workloads.standard(name, 0))
+        take = np.array([0, 3, 11, 40] if name != "PSL(2,11)" else [0, 9])
+        x, z = philox.sample_errors(philox.NOISE_DEPOL, p, 21 + c, take, oc.n)
+        sel = np.nonzero(code_of == c)[0]
+        for side, e in ((0, x), (1, z)):
+            wc, wst, _, _ = olead.decode(oc, side, philox.syndromes(oc.sides[side].H, e), 2 * p / 3)
+            for k, i in enumerate(take):
+                r = int(np.nonzero(res["id"] == sel[i])[0][0])
+                assert res["status"][r][side] == wst[k]
+                got = philox.unpack_bits(cor[r:r + 1, side, :codes[c].info.words_n], oc.n)[0]
+                assert (got == wc[k]).all()
 
 
 def test_alone_equals_in_the_mix(setup):
     lead, serving, codes, rows, ref, p = setup
-    srv = lead.Server(codes, [2 * p / 3] * 2, max_batch=32, streams=2, budget_bytes=256 << 20)
-    for c in (0, 1):
+    srv = lead.Server(codes, [2 * p / 3] * 3, max_batch=32, streams=2, budget_bytes=256 << 20)
+    for c in range(len(codes)):
         for i in (0, 7, 42):
             srv.submit(c, rows[c][i:i + 1], np.array([1000 * c + i], dtype=np.uint64))
             got = []
@@ -89,11 +109,12 @@ def test_alone_equals_in_the_mix(setup):
 def test_memory_admission(setup):
     lead, serving, codes, rows, ref, p = setup
     with pytest.raises(lead.LeadError) as e:
-        lead.Server(codes, [2 * p / 3] * 2, max_batch=1024, streams=4, budget_bytes=1 << 16)
+        lead.Server(codes, [2 * p / 3] * 3, max_batch=1024, streams=4, budget_bytes=1 << 16)
     assert e.value.rc == -5           # LEAD_EOOM: not even one slot fits the budget
     # a small budget admits fewer slots and still serves every request
-    srv = lead.Server(codes, [2 * p / 3] * 2, max_batch=8, streams=4, budget_bytes=400_000)
+    srv = lead.Server(codes, [2 * p / 3] * 3, max_batch=8, streams=4, budget_bytes=400_000)
     arrival, _ = serving.poisson_trace(1e5, 20, [1.0], np.random.default_rng(1))
-    res, cor = serving.run_trace(srv, [rows[0][:20], rows[1][:0]], arrival, np.zeros(20, dtype=np.int32))
+    res, cor = serving.run_trace(srv, [rows[0][:20], rows[1][:0], rows[2][:0]], arrival,
+                                 np.zeros(20, dtype=np.int32))
     _check(res, cor, codes, ref, lambda rid: (0, rid))
     srv.close()

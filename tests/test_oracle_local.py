@@ -150,34 +150,68 @@ def test_posterior_fourier_form_fp64(psl7):
             assert abs((1 - Tj / T) / 2 - q[s, j]) < 1e-12
 
 
-def test_log_series_f64_accuracy():
-    rng = np.random.default_rng(0)
-    x = np.concatenate([np.exp(rng.uniform(-40, 40, 100000)), [1.0, 2.0, 0.5, np.sqrt(2.0)]])
-    got = local.log_series_f64(x)
-    ref = np.log(x)
-    assert np.abs(got - ref).max() <= 4e-15 * np.maximum(1.0, np.abs(ref)).max()
+def _f32_round_exact(x, Fraction):
+    """Binary32 nearest (ties to even) to the rational x, by exact comparison with the midpoints
+    of its two binary32 neighbours."""
+    est = np.float32(float(x))
+    cands = [np.nextafter(est, np.float32(-np.inf), dtype=np.float32), est,
+             np.nextafter(est, np.float32(np.inf), dtype=np.float32)]
+    dist = [abs(Fraction(float(c)) - x) for c in cands]
+    best = min(range(3), key=lambda k: (dist[k], int(cands[k].view(np.uint32)) & 1))
+    return cands[best]
 
 
-def test_llr_f32_matches_fp64():
-    """The interpolated binary32 LLR stays within 2e-5 of ln((1-p)/p) on the whole clamp range,
-    and within its interpolation bound (p/128)^2 / (8 p^2) + rounding."""
-    p = np.concatenate([np.geomspace(2.0 ** -23, 0.5, 200001), np.linspace(0.5, 1 - 2.0 ** -23, 100001)])
-    p32 = p.astype(np.float32)
-    got = local.llr_f32(p32).astype(np.float64)
-    q = np.clip(p32.astype(np.float64), 2.0 ** -23, 1 - 2.0 ** -23)
-    ref = np.log((1 - q) / q)
-    assert np.abs(got - ref).max() < 2e-5
-    # lambda(p) = -lambda(1 - p) exactly for p > 1/2, where 1 - p is exact in binary32
+def test_llr_f32_is_the_rounded_exact_value():
+    """lambda(p) = ln((1-p)/p) rounded to binary32, checked against ln(1-p) - ln(p) evaluated at
+    60 digits by mpmath (another identity and another library than the oracle's) and rounded by
+    exact rational comparison, on log-uniform p over the clamp range, p near 1/2 and near 2^-23."""
+    mpmath = pytest.importorskip("mpmath")
+    from fractions import Fraction
+    mpmath.mp.dps = 60
+    rng = np.random.default_rng(12)
+    p = np.concatenate([np.exp2(rng.uniform(-23, -1, 1500)),
+                        0.5 - np.exp2(rng.uniform(-24, -3, 400)),
+                        np.float32(2.0 ** -23) * (1 + rng.integers(0, 4096, 100).astype(np.float64) * 2.0 ** -23),
+                        [2.0 ** -23, 0.25, 0.5, 0.125, 0.01, 0.05]]).astype(np.float32)
+    got = local.llr_f32(p)
+    for pi, gi in zip(p, got):
+        mp = mpmath.mpf(float(pi))
+        exact = mpmath.log(1 - mp) - mpmath.log(mp)
+        want = _f32_round_exact(Fraction(mpmath.nstr(exact, 55, min_fixed=-100, max_fixed=100)), Fraction)
+        assert gi.view(np.uint32) == want.view(np.uint32), (float(pi), float(gi), float(want))
+
+
+def test_llr_f32_exact_fallback_matches_mpmath():
+    """The decimal fallback the oracle uses near rounding boundaries gives the same rounding as
+    mpmath's logarithm, on random inputs (it is exercised here directly, since boundary cases
+    are rare)."""
+    mpmath = pytest.importorskip("mpmath")
+    from fractions import Fraction
+    mpmath.mp.dps = 60
+    rng = np.random.default_rng(13)
+    for pi in np.exp2(rng.uniform(-23, -1, 200)).astype(np.float32):
+        mp = mpmath.mpf(float(pi))
+        exact = mpmath.log((1 - mp) / mp)
+        want = _f32_round_exact(Fraction(mpmath.nstr(exact, 55, min_fixed=-100, max_fixed=100)), Fraction)
+        assert local._llr_exact_round(pi).view(np.uint32) == want.view(np.uint32)
+
+
+def test_llr_f32_symmetry_and_fixed_values():
+    """lambda(1/2) = 0; lambda(1 - p) = -lambda(p) exactly (1 - p is exact for p > 1/2);
+    lambda(1/4) = ln 3 and lambda(2^-k) = ln(2^k - 1) rounded; strictly decreasing on a grid;
+    the clamp maps p <= 0 and p >= 1 to the ends of [2^-23, 1 - 2^-23]."""
+    assert local.llr_f32(np.array([0.5], dtype=np.float32))[0] == 0.0
     s = np.linspace(0.5, 1 - 2.0 ** -23, 1001)[1:].astype(np.float32)
     assert (local.llr_f32(s) == -local.llr_f32((np.float32(1) - s).astype(np.float32))).all()
-
-
-def test_llr_nodes_hit_exactly():
-    T0, T1 = local.llr_tables()
-    i = np.arange(local.LLR_NODES, dtype=np.uint32)
-    nodes = ((i + np.uint32(local.LLR_NODE0)) << np.uint32(16)).view(np.float32)
-    assert (local.llr_f32(nodes) == T0).all()
-    assert T0[-1] == 0.0                       # lambda(1/2) = 0
+    assert local.llr_f32(np.array([0.25], dtype=np.float32))[0] == np.float32(np.log(3.0))
+    for k in (1, 2, 5, 10, 20, 23):
+        assert local.llr_f32(np.array([2.0 ** -k], dtype=np.float32))[0] == np.float32(np.log(2.0 ** k - 1.0))
+    g = np.geomspace(2.0 ** -23, 1 - 2.0 ** -23, 100001).astype(np.float32)
+    g = np.unique(g)
+    assert (np.diff(local.llr_f32(g).astype(np.float64)) < 0).all()
+    ends = local.llr_f32(np.array([0.0, -1.0, 1.0, 2.0], dtype=np.float32))
+    lo, hi = local.llr_f32(np.array([2.0 ** -23, 1 - 2.0 ** -23], dtype=np.float32))
+    assert (ends == np.array([lo, lo, hi, hi], dtype=np.float32)).all()
 
 
 def test_boost_applies_to_ml_bits(psl7):
