@@ -15,8 +15,12 @@
 // A tile is 128 items = the MMA's M = the tensor-memory lanes. R' is split into two binary16
 // terms (22 significant bits; the exact 0/1 incidence makes each product exact) and W into two
 // bfloat16 terms (16 significant bits over binary32's exponent range), with binary32
-// accumulation in tensor memory. The coset is taken in chunks of up to 128 members (GEMM1's N),
-// each with its own maximum; the chunks' accumulators are combined at the end.
+// accumulation in tensor memory. The coset is taken in chunks of up to 128 members (GEMM1's N)
+// that all add into one accumulator. The normaliser is the score of the least-cost member: a
+// class's log-sum exceeds its best pattern's log-weight by at most log2 of the class size, and
+// the least-cost member takes the best pattern of every row, so no member's score exceeds it by
+// more than Delta log2(2^Delta / 2^kB) (18 for Delta = 6): every W is at most 2^18, and the
+// least-cost member's own W is 1.
 //
 // On the CUDA cores: the prior LLRs, the class log-sums and shares (log-sum-exp in binary32),
 // the least-cost local decision (exact integer costs W_ab = rint(2^20 lambda_ab), ties to the
@@ -54,10 +58,9 @@ struct TcShape {
   static constexpr int CW = CH / HC;              // members per thread in the chunk epilogue
   static constexpr int RH = DELTA / 2;            // rows per thread
   static constexpr int MPT = NK / 2;              // members per thread in the least-cost search
-  // tensor memory: the chunk's scores in [0, CH), accumulator c at AGG0 + c * AGG_STRIDE
+  // tensor memory: the chunk's scores in [0, CH), the accumulator at AGG0
   static constexpr int AGG0 = CH < 32 ? 32 : CH;
-  static constexpr int AGG_STRIDE = 64;
-  static constexpr int TM_USED = AGG0 + NCH * AGG_STRIDE;
+  static constexpr int TM_USED = AGG0 + (K1 < 32 ? 32 : 64);
   static constexpr int TM_COLS = TM_USED <= 32 ? 32 : TM_USED <= 64 ? 64 : TM_USED <= 128 ? 128
                                  : TM_USED <= 256 ? 256 : 512;
   static constexpr int CSTR = K1 + 1;             // int32 words per item in the cost table
@@ -75,8 +78,7 @@ struct TcShape {
   static constexpr size_t XMIN = COST + (size_t)kTile * CSTR * 4;  // 128 x XSTR uint8
   static constexpr size_t KERN = (XMIN + (size_t)kTile * XSTR + 15) & ~size_t(15);   // NK uint32
   static constexpr size_t BEST = KERN + (size_t)NK * 4;            // 2 x 128 (cost, member) int2
-  static constexpr size_t MAXS = BEST + 2 * (size_t)kTile * 8;     // (NCH + 1) x 2 x 128 float
-  static constexpr size_t XCLS = MAXS + (size_t)(NCH + 1) * 2 * kTile * 4;   // NX uint8
+  static constexpr size_t XCLS = BEST + 2 * (size_t)kTile * 8;     // NX uint8
   static constexpr size_t BYTES = (XCLS + NX + 15) & ~size_t(15);
   static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
   static_assert(CH % 16 == 0 && K1 % 16 == 0 && CW % 16 == 0, "MMA shapes");
@@ -110,6 +112,31 @@ __device__ __forceinline__ uint32_t pack_bf162(float lo, float hi) {
 template <int NX>
 __device__ __forceinline__ int scr_index(int tid, int x) {
   return tid * NX + (x ^ ((tid & 31) & (NX - 1)));
+}
+
+// 2^x by the hardware's approximate base-2 exponential (ex2.approx.ftz, relative error about
+// 2^-22; results below 2^-126 flush to 0, far below every sum they enter here).
+__device__ __forceinline__ float fast_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// v[g] <- v[g ^ p] for a runtime p in [0, N): one conditional swap stage per bit of p, so the
+// array stays in registers.
+template <int N>
+__device__ __forceinline__ void xor_permute(float (&v)[N], uint32_t p) {
+#pragma unroll
+  for (int bit = 1; bit < N; bit <<= 1) {
+    const bool sw = (p & (uint32_t)bit) != 0;
+#pragma unroll
+    for (int g = 0; g < N; ++g) {
+      if (g & bit) continue;
+      const float x = v[g], y = v[g | bit];
+      v[g] = sw ? y : x;
+      v[g | bit] = sw ? x : y;
+    }
+  }
 }
 
 __host__ __device__ constexpr int lowest_bit(int x) { return (x & 1) ? 0 : 1 + lowest_bit(x >> 1); }
@@ -148,7 +175,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
   int* cost_s = reinterpret_cast<int*>(sm + S::COST);
   uint8_t* xmin_s = sm + S::XMIN;
   int2* best_s = reinterpret_cast<int2*>(sm + S::BEST);
-  float* maxs_s = reinterpret_cast<float*>(sm + S::MAXS);
 
   // ---- once per CTA: coset tables and the two incidence operands (exact 0/1) ----
   for (int i = tid; i < NK; i += kTcThreads) kern_s[i] = __ldg(a.ckern + i);
@@ -188,17 +214,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
         tc::mma_f16(tbase, ad, bd, idesc1, t > 0 || ks > 0);
       }
   };
-  // GEMM2 of chunk c: acc_c[item][(a, g)] = sum over the chunk's members of W x incidence (two terms of W)
+  // GEMM2 of chunk c: acc[item][(a, g)] += the chunk's W times the incidence (two terms of W)
   auto issue_gemm2 = [&](int c) {
     const uint32_t a2 = tc::smem_addr(sm + S::A2), b2 = tc::smem_addr(sm + S::B2);
-    const uint32_t d = tbase + (uint32_t)(S::AGG0 + c * S::AGG_STRIDE);
 #pragma unroll
     for (int t = 0; t < 2; ++t)
 #pragma unroll
       for (int ks = 0; ks < CH / 16; ++ks) {
         const uint64_t ad = tc::smem_desc(a2 + (uint32_t)(t * S::A2_TERM) + (uint32_t)(ks * 2 * kTile * 16), kTile * 16, 128);
         const uint64_t bd = tc::smem_desc(b2 + (uint32_t)(((c * CH + ks * 16) / 8) * (K1 * 16)), K1 * 16, 128);
-        tc::mma_f16(d, ad, bd, idesc2, t > 0 || ks > 0);
+        tc::mma_f16(tbase + (uint32_t)S::AGG0, ad, bd, idesc2, c > 0 || t > 0 || ks > 0);
       }
   };
   auto wait_or_abort = [&](uint64_t* mbar, uint32_t& ph) {
@@ -207,6 +232,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
       if (a.err) atomicOr(a.err, 1u);
     }
     ph ^= 1u;
+  };
+  // key of coset member i for this item: the least-cost pattern of every row, row a at bit a*Delta
+  auto key_of = [&](int i) {
+    const uint32_t k = kern_s[i];
+    const uint8_t* xrow = xmin_s + row * S::XSTR;
+    unsigned long long key = 0;
+#pragma unroll
+    for (int ra = 0; ra < DELTA; ++ra)
+      key |= (unsigned long long)xrow[ra * NF + ((k >> (ra * KB)) & (NF - 1))] << (ra * DELTA);
+    return key;
   };
 
   const int64_t ntiles = (a.items + kTile - 1) / kTile;
@@ -217,26 +252,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
     const int v = active ? (int)(item - shot * a.order) : 0;
     const uint32_t s = active ? bit_field(a.syn + shot * a.words_m, v * ML, ML) : 0u;
     const uint32_t fb = __ldg(a.cbase + s);
+    const float* lam_row = a.lam + shot * a.n;
+    const uint16_t* vrow = a.views + v * NL;
 
     // ---- this thread's rows: prior LLRs (log2 units), integer costs, class log-sums, least-cost
     // patterns; the R' operand (two binary16 terms) and the permuted cost / pattern tables ----
-    float wl[S::RH][DELTA];
-    int Wc[S::RH][DELTA];
-#pragma unroll
-    for (int rr = 0; rr < S::RH; ++rr) {
-      const int ra = half * S::RH + rr;
-#pragma unroll
-      for (int b = 0; b < DELTA; ++b) {
-        const int q = __ldg(a.views + v * NL + b * DELTA + ra);
-        const float lam = active ? __ldg(a.lam + shot * a.n + q) : 0.0f;
-        wl[rr][b] = lam * kLog2e;
-        Wc[rr][b] = __float2int_rn(__fmul_rn(lam, 1048576.0f));
-      }
-    }
 #pragma unroll 1
     for (int rr = 0; rr < S::RH; ++rr) {
       const int ra = half * S::RH + rr;
-      row_weights<DELTA>(scr, tid, wl[rr]);
+      float wl[DELTA];
+      int Wc[DELTA];
+#pragma unroll
+      for (int b = 0; b < DELTA; ++b) {
+        const float lam = active ? __ldg(lam_row + __ldg(vrow + b * DELTA + ra)) : 0.0f;
+        wl[b] = lam * kLog2e;
+        Wc[b] = __float2int_rn(__fmul_rn(lam, 1048576.0f));
+      }
+      row_weights<DELTA>(scr, tid, wl);
       const uint32_t fba = (fb >> (ra * KB)) & (NF - 1);
       float R[NF];
 #pragma unroll
@@ -249,7 +281,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
           m = fmaxf(m, scr[scr_index<NX>(tid, x)]);
           int c = 0;
 #pragma unroll
-          for (int b = 0; b < DELTA; ++b) c += ((x >> b) & 1) ? Wc[rr][b] : 0;
+          for (int b = 0; b < DELTA; ++b) c += ((x >> b) & 1) ? Wc[b] : 0;
           if (c < cmin) {                 // the class lists patterns in increasing order
             cmin = c;
             xmin = x;
@@ -257,7 +289,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
         }
         float sum = 0.0f;
 #pragma unroll
-        for (int t = 0; t < CS; ++t) sum += exp2f(scr[scr_index<NX>(tid, xcls_s[f * CS + t])] - m);
+        for (int t = 0; t < CS; ++t) sum += fast_exp2(scr[scr_index<NX>(tid, xcls_s[f * CS + t])] - m);
         R[f] = m + __log2f(sum);
         const int g = f ^ (int)fba;
         cost_s[row * S::CSTR + ra * NF + g] = cmin;
@@ -266,11 +298,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
       float rmax = -INFINITY;
 #pragma unroll
       for (int f = 0; f < NF; ++f) rmax = fmaxf(rmax, R[f]);
-      // R'[(ra, g)] = R[g ^ fba] - rmax as two binary16 terms, NF consecutive K columns
+      xor_permute<NF>(R, fba);            // R[g] = log-sum of class g ^ fba
+      // R'[(ra, g)] = R[g] - rmax as two binary16 terms, NF consecutive K columns
       uint32_t hi[NF / 2], lo[NF / 2];
 #pragma unroll
       for (int g = 0; g < NF; g += 2) {
-        const float v0 = active ? R[g ^ fba] - rmax : 0.0f, v1 = active ? R[(g + 1) ^ fba] - rmax : 0.0f;
+        const float v0 = active ? R[g] - rmax : 0.0f, v1 = active ? R[g + 1] - rmax : 0.0f;
         const float h0 = __half2float(__float2half_rn(v0)), h1 = __half2float(__float2half_rn(v1));
         hi[g / 2] = pack_half2(v0, v1);
         lo[g / 2] = pack_half2(v0 - h0, v1 - h1);
@@ -295,19 +328,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
     }
 
     // ---- least-cost local decision over this thread's half of the coset (overlaps the MMAs) ----
-    int best = INT_MAX, bi = half * S::MPT;
     {
+      int best = INT_MAX, bi = half * S::MPT;
       const int* crow = cost_s + row * S::CSTR;
-      const uint8_t* xrow = xmin_s + row * S::XSTR;
-      auto key_of = [&](int i) {
-        const uint32_t k = kern_s[i];
-        unsigned long long key = 0;
-#pragma unroll
-        for (int ra = 0; ra < DELTA; ++ra)
-          key |= (unsigned long long)xrow[ra * NF + ((k >> (ra * KB)) & (NF - 1))] << (ra * DELTA);
-        return key;
-      };
-#pragma unroll 4
+#pragma unroll 2
       for (int i0 = 0; i0 < S::MPT; ++i0) {
         const int i = half * S::MPT + i0;
         const uint32_t k = kern_s[i];
@@ -323,74 +347,68 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
       }
       best_s[half * kTile + row] = make_int2(best, bi);
     }
+    __syncthreads();
+    // the least-cost member over both halves: (cost, key), lexicographic; its score (from the R'
+    // operand, as the tensor cores see it) is the normaliser of W
+    int ml_member;
+    {
+      const int2 b0 = best_s[row], b1 = best_s[kTile + row];
+      const bool second = b1.x < b0.x || (b1.x == b0.x && key_of(b1.y) < key_of(b0.y));
+      ml_member = second ? b1.y : b0.y;
+    }
+    float M = 0.0f;
+    {
+      const uint32_t k = kern_s[ml_member];
+#pragma unroll
+      for (int ra = 0; ra < DELTA; ++ra) {
+        const uint32_t off = tc::kmajor_offset(row, ra * NF + (int)((k >> (ra * KB)) & (NF - 1)), kTile);
+        M += __half2float(__ushort_as_half(*reinterpret_cast<const uint16_t*>(sm + S::A1 + off))) +
+             __half2float(__ushort_as_half(*reinterpret_cast<const uint16_t*>(sm + S::A1 + S::A1_TERM + off)));
+      }
+    }
 
-    // ---- chunks: scores -> chunk maximum -> W (two bfloat16 terms) -> GEMM2 ----
-    float mx[S::NCH];
+    // ---- chunks: scores -> W = 2^(score - M) (two bfloat16 terms) -> GEMM2 ----
 #pragma unroll 1
     for (int c = 0; c < S::NCH; ++c) {
       wait_or_abort(&mbar_g1, ph_g1);
+      if (c > 0) wait_or_abort(&mbar_g2, ph_g2);   // the previous GEMM2 has read A2
       tc::fence_after_sync();
       const bool mine = S::HC == 2 || half == 0;
       const int col0 = S::HC == 2 ? half * CW : 0;
-      float sc[CW];
       if (mine && !abort_s) {
 #pragma unroll
-        for (int j = 0; j < CW; j += 32) {
-          if constexpr (CW % 32 == 0) {
-            float t32[32];
-            tc::tmem_ld32(tbase + lane_base + (uint32_t)(col0 + j), t32);
+        for (int j = 0; j < CW; j += 16) {
+          float sc[16];
+          tc::tmem_ld16(tbase + lane_base + (uint32_t)(col0 + j), sc);
 #pragma unroll
-            for (int u = 0; u < 32; ++u) sc[j + u] = t32[u];
-          } else {
-            float t16[16];
-            tc::tmem_ld16(tbase + lane_base + (uint32_t)(col0 + j), t16);
+          for (int h8 = 0; h8 < 16; h8 += 8) {
+            uint32_t hi[4], lo[4];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) sc[j + u] = t16[u];
+            for (int u = 0; u < 8; u += 2) {
+              const float w0 = fast_exp2(sc[h8 + u] - M), w1 = fast_exp2(sc[h8 + u + 1] - M);
+              const float g0 = __bfloat162float(__float2bfloat16_rn(w0));
+              const float g1 = __bfloat162float(__float2bfloat16_rn(w1));
+              hi[u / 2] = pack_bf162(w0, w1);
+              lo[u / 2] = pack_bf162(w0 - g0, w1 - g1);
+            }
+            unsigned char* p0 = sm + S::A2 + tc::kmajor_offset(row, col0 + j + h8, kTile);
+            *reinterpret_cast<uint4*>(p0) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(p0 + S::A2_TERM) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
           }
-        }
-      }
-      float m = -INFINITY;
-      if (mine) {
-#pragma unroll
-        for (int j = 0; j < CW; ++j) m = fmaxf(m, sc[j]);
-      }
-      maxs_s[(c & 1) * 2 * kTile + half * kTile + row] = m;
-      tc::fence_before_sync();
-      __syncthreads();                     // every score of the chunk read; both maxima posted
-      if (abort_s) break;
-      m = fmaxf(maxs_s[(c & 1) * 2 * kTile + row], maxs_s[(c & 1) * 2 * kTile + kTile + row]);
-      mx[c] = m;
-      if (tid == 0 && c + 1 < S::NCH) {    // the next chunk's scores overwrite this chunk's
-        tc::fence_after_sync();
-        issue_gemm1(c + 1);
-        tc::mma_commit(&mbar_g1);
-      }
-      if (c > 0) wait_or_abort(&mbar_g2, ph_g2);   // the previous GEMM2 has read A2
-      if (mine) {
-#pragma unroll
-        for (int j = 0; j < CW; j += 8) {
-          uint32_t hi[4], lo[4];
-#pragma unroll
-          for (int u = 0; u < 8; u += 2) {
-            const float w0 = exp2f(sc[j + u] - m), w1 = exp2f(sc[j + u + 1] - m);
-            const float h0 = __bfloat162float(__float2bfloat16_rn(w0));
-            const float h1 = __bfloat162float(__float2bfloat16_rn(w1));
-            hi[u / 2] = pack_bf162(w0, w1);
-            lo[u / 2] = pack_bf162(w0 - h0, w1 - h1);
-          }
-          unsigned char* p0 = sm + S::A2 + tc::kmajor_offset(row, col0 + j, kTile);
-          *reinterpret_cast<uint4*>(p0) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<uint4*>(p0 + S::A2_TERM) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
       }
       tc::fence_async_smem();
       tc::fence_before_sync();
-      __syncthreads();
+      __syncthreads();                     // scores of the chunk read, its W in place
       if (abort_s) break;
       if (tid == 0) {
         tc::fence_after_sync();
         issue_gemm2(c);
         tc::mma_commit(&mbar_g2);
+        if (c + 1 < S::NCH) {
+          issue_gemm1(c + 1);
+          tc::mma_commit(&mbar_g1);
+        }
       }
     }
     if (abort_s) break;
@@ -399,62 +417,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
     __syncthreads();
     if (abort_s) break;
 
-    // ---- combine the chunks, least-cost decision, marginals, boost, store ----
-    float M = -INFINITY;
-#pragma unroll
-    for (int c = 0; c < S::NCH; ++c) M = fmaxf(M, mx[c]);
-    float agg[S::RH][NF];
-#pragma unroll
-    for (int rr = 0; rr < S::RH; ++rr)
-#pragma unroll
-      for (int g = 0; g < NF; ++g) agg[rr][g] = 0.0f;
-#pragma unroll 1
-    for (int c = 0; c < S::NCH; ++c) {
-      const float sc = exp2f(mx[c] - M);
-      const uint32_t col = (uint32_t)(S::AGG0 + c * S::AGG_STRIDE);
-      float acc[K1];
-#pragma unroll
-      for (int j = 0; j < K1; j += 16) {
-        float t16[16];
-        tc::tmem_ld16(tbase + lane_base + col + (uint32_t)j, t16);
-#pragma unroll
-        for (int u = 0; u < 16; ++u) acc[j + u] = t16[u];
-      }
-#pragma unroll
-      for (int rr = 0; rr < S::RH; ++rr)
-#pragma unroll
-        for (int g = 0; g < NF; ++g) agg[rr][g] += acc[(half * S::RH + rr) * NF + g] * sc;
-    }
-    float Z = 0.0f;
-#pragma unroll
-    for (int g = 0; g < NF; ++g) Z += agg[0][g];
-    // the least-cost member over both halves: (cost, key), lexicographic
+    // ---- marginals, boost, store ----
     unsigned long long mask = 0;
     {
-      const int2 b0 = best_s[row], b1 = best_s[kTile + row];
-      const uint8_t* xrow = xmin_s + row * S::XSTR;
-      auto key_of = [&](int i) {
-        const uint32_t k = kern_s[i];
-        unsigned long long key = 0;
-#pragma unroll
-        for (int ra = 0; ra < DELTA; ++ra)
-          key |= (unsigned long long)xrow[ra * NF + ((k >> (ra * KB)) & (NF - 1))] << (ra * DELTA);
-        return key;
-      };
-      const unsigned long long k0 = key_of(b0.y), k1 = key_of(b1.y);
-      const unsigned long long key = (b1.x < b0.x || (b1.x == b0.x && k1 < k0)) ? k1 : k0;
+      const unsigned long long key = key_of(ml_member);
 #pragma unroll
       for (int ra = 0; ra < DELTA; ++ra)
 #pragma unroll
-        for (int b = 0; b < DELTA; ++b)
-          mask |= ((key >> (ra * DELTA + b)) & 1ull) << (b * DELTA + ra);
+        for (int b = 0; b < DELTA; ++b) mask |= ((key >> (ra * DELTA + b)) & 1ull) << (b * DELTA + ra);
     }
-    const float rz = 1.0f / Z;
+    float rz = 0.0f;
 #pragma unroll 1
     for (int rr = 0; rr < S::RH; ++rr) {
       const int ra = half * S::RH + rr;
-      row_weights<DELTA>(scr, tid, wl[rr]);
+      float wl[DELTA];
+#pragma unroll
+      for (int b = 0; b < DELTA; ++b)
+        wl[b] = (active ? __ldg(lam_row + __ldg(vrow + b * DELTA + ra)) : 0.0f) * kLog2e;
+      row_weights<DELTA>(scr, tid, wl);
       const uint32_t fba = (fb >> (ra * KB)) & (NF - 1);
+      float agg[NF];
+      {
+        float t16[16];
+        tc::tmem_ld16(tbase + lane_base + (uint32_t)(S::AGG0 + (ra * NF) / 16 * 16), t16);
+        const int off = (ra * NF) % 16;    // the row's NF columns within the 16 loaded
+#pragma unroll
+        for (int g = 0; g < NF; ++g) {
+          agg[g] = t16[g];
+#pragma unroll
+          for (int o = NF; o < 16; o += NF)
+            if (off == o) agg[g] = t16[o + g];
+        }
+      }
+      if (rr == 0) {                       // every row's classes partition the coset: Z
+        float Z = 0.0f;
+#pragma unroll
+        for (int g = 0; g < NF; ++g) Z += agg[g];
+        rz = 1.0f / Z;
+      }
+      xor_permute<NF>(agg, fba);           // agg[f] = weight of the members whose row ra is in class f
       float qb[DELTA];
 #pragma unroll
       for (int b = 0; b < DELTA; ++b) qb[b] = 0.0f;
@@ -469,12 +470,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
 #pragma unroll
         for (int t = 0; t < CS; ++t) {
           const int x = xcls_s[f * CS + t];
-          const float e = exp2f(scr[scr_index<NX>(tid, x)] - m);
+          const float e = fast_exp2(scr[scr_index<NX>(tid, x)] - m);
           sum += e;
 #pragma unroll
           for (int b = 0; b < DELTA; ++b) tb[b] += ((x >> b) & 1) ? e : 0.0f;
         }
-        const float wgt = agg[rr][f ^ (int)fba] / sum;
+        const float wgt = agg[f] / sum;
 #pragma unroll
         for (int b = 0; b < DELTA; ++b) qb[b] += wgt * tb[b];
       }
