@@ -135,9 +135,18 @@ lead_bp_jit(const lead::BPJitArgs a) {
   msg_t* Us = reinterpret_cast<msg_t*>(smem);
   msg_t* Ps = Us + NL * TS;
   msg_t* Ls = Ps + NL * TS;
+#if LEAD_ALIAS
+  // one shot per CTA: the staged syndromes live in the posterior array (read by the prologue
+  // only, before the first iteration writes posteriors) and the correction bits in the prior
+  // array (dead once the shot has stopped)
+  unsigned int* syn_s = reinterpret_cast<unsigned int*>(Ps);
+  unsigned int* cb = reinterpret_cast<unsigned int*>(Ls);
+  int* flags = nullptr;
+#else
   unsigned int* syn_s = smem + kMsgBytes / 4;
   unsigned int* cb = syn_s + spb * wm;
   int* flags = reinterpret_cast<int*>(cb + spb * a.words_n);
+#endif
   const unsigned short* __restrict__ PA = a.pa;
 
   const int tid = threadIdx.x;
@@ -149,8 +158,10 @@ lead_bp_jit(const lead::BPJitArgs a) {
   for (long long g0 = (long long)blockIdx.x * spb; g0 < a.shots; g0 += (long long)gridDim.x * spb) {
     const int nsh = (int)((a.shots - g0) < spb ? (a.shots - g0) : spb);
     for (int i = tid; i < nsh * wm; i += blockDim.x) syn_s[i] = __ldg(a.syn + g0 * wm + i);
+#if !LEAD_ALIAS
     for (int i = tid; i < spb * a.words_n; i += blockDim.x) cb[i] = 0u;
     if (tid < 2 * spb) flags[tid] = 0;
+#endif
     __syncthreads();
     const bool act = lane_ok && sl < nsh;
     RowMag mag[ML];
@@ -212,6 +223,12 @@ lead_bp_jit(const lead::BPJitArgs a) {
         __syncthreads();
         conv = flags[(t & 1) * spb + sl] == 0;
       }
+#if LEAD_ALIAS
+      if (conv || t >= a.max_iter) {      // uniform: the prior array now takes the correction bits
+        for (int i = tid; i < a.words_n; i += blockDim.x) cb[i] = 0u;
+        __syncthreads();
+      }
+#endif
       if (!mydone && (conv || t >= a.max_iter)) {
         const long long shot = g0 + sl;
         for (int j = 0; j < NL; ++j) {
@@ -379,9 +396,17 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
   msg_t* Us = reinterpret_cast<msg_t*>(smem);
   msg_t* Ps = Us + NL * TS;
   msg_t* Ls = Ps + NL * TS;
+#if LEAD_ALIAS
+  // the staged syndromes live in the posterior array and the correction bits in the prior array
+  // (see the single-CTA kernel); the two verdict words follow the messages
+  unsigned int* syn_s = reinterpret_cast<unsigned int*>(Ps);
+  unsigned int* cb = reinterpret_cast<unsigned int*>(Ls);
+  unsigned int* flags = smem + kMsgBytes / 4;    // two words, meaningful in rank 0 only
+#else
   unsigned int* syn_s = smem + kMsgBytes / 4;
   unsigned int* cb = syn_s + wm;
   unsigned int* flags = cb + a.words_n;          // two words, meaningful in rank 0 only
+#endif
 
   const unsigned int rank = cluster_rank();
   const int tid = threadIdx.x;
@@ -397,7 +422,9 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
 
   for (long long g0 = cid; g0 < a.shots; g0 += ncl) {
     for (int i = tid; i < wm; i += blockDim.x) syn_s[i] = __ldg(a.syn + g0 * wm + i);
+#if !LEAD_ALIAS
     for (int i = tid; i < a.words_n; i += blockDim.x) cb[i] = 0u;
+#endif
     if (tid < 2) flags[tid] = 0u;
     RowMag mag[ML];
     unsigned int meta[ML];
@@ -511,6 +538,11 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
       cluster_wait();
       const bool conv = ld_cluster_u32(flag0 + 4u * (t & 1)) == 0u;
       if (conv || t >= a.max_iter) {
+#if LEAD_ALIAS
+        // this CTA's priors are dead (its gathers of this iteration are done): correction bits
+        for (int i = tid; i < a.words_n; i += blockDim.x) cb[i] = 0u;
+        __syncthreads();
+#endif
         if (lane_ok) {
           for (int j = 0; j < NL; ++j) {
             if (cluster_partner(a.pa, j, v, V).first) {

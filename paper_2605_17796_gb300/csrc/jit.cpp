@@ -32,9 +32,20 @@ static size_t msg_bytes(int prec) { return prec == LEAD_PREC_FP32 ? 4 : 2; }
 Geometry bp_geometry(const lead_code* code, int side, int prec) {
   const SideParams& P = code->side[side].params;
   Geometry g{};
+  // With one shot per CTA (or per cluster) the staged syndrome row lives in the posterior array
+  // (which the first iteration writes only after the prologue has read the syndromes) and the
+  // correction bits in the prior array (dead once the shot has stopped); only the cluster
+  // kernel's two verdict words follow the messages.
+  // (the posterior and prior arrays start at multiples of one array's bytes, which must keep
+  // the 4-byte alignment of the words stored there)
+  auto aliased = [&](int ts, int spb, size_t mb) {
+    const size_t region = (size_t)ts * code->nl * mb;     // one of the three message arrays
+    return spb == 1 && region % 4 == 0 && region >= sizeof(uint32_t) * std::max<size_t>(P.words_m, code->words_n);
+  };
   auto smem_for = [&](int ts, int spb, size_t mb) {
     const size_t msgs = ((size_t)ts * code->nl * 3 * mb + 15) & ~size_t(15);
-    return msgs + sizeof(uint32_t) * ((size_t)spb * P.words_m + (size_t)spb * code->words_n + 2 * (size_t)spb);
+    if (aliased(ts, spb, mb)) return msgs + 16;
+    return msgs + sizeof(uint32_t) * ((size_t)spb * P.words_m + (size_t)spb * code->words_n + 2 * (size_t)spb + 2);
   };
   // The split of shots and vertices over CTAs is fixed by the binary32 footprint, so every
   // precision mode shares one partner table; the 16-bit modes only need less shared memory.
@@ -51,11 +62,13 @@ Geometry bp_geometry(const lead_code* code, int side, int prec) {
     smem32 = smem_for(g.ts, 1, 4);
   }
   g.smem = smem_for(g.ts, g.spb, msg_bytes(prec));
+  g.alias = aliased(g.ts, g.spb, msg_bytes(prec));
   g.block = (g.ts + 31) / 32 * 32;
   // CTAs per SM that shared memory allows (227 KB usable, 1 KB reserved per CTA), capped so
-  // that each thread keeps at least 64 registers
+  // that each thread keeps at least 48 registers (compile_one steps down while the register cap
+  // this implies makes the compiler spill)
   int by_smem = (int)((227u * 1024u) / (g.smem + 1024));
-  int by_regs = 65536 / (g.block * 64);
+  int by_regs = 65536 / (g.block * 48);
   g.minblocks = std::max(1, std::min(by_smem, by_regs));
   return g;
 }
@@ -79,7 +92,8 @@ std::string prelude(const lead_code* code, int side, const Geometry& g, int prec
     << "#define LEAD_SPB " << g.spb << "\n"
     << "#define LEAD_CLUSTER " << g.cluster << "\n"
     << "#define LEAD_PREC " << prec << "\n"
-    << "#define LEAD_PA16 " << (cluster_pa16(g, code->nl) ? 1 : 0) << "\n";
+    << "#define LEAD_PA16 " << (cluster_pa16(g, code->nl) ? 1 : 0) << "\n"
+    << "#define LEAD_ALIAS " << (g.alias ? 1 : 0) << "\n";
   // the local rows touching every slot j (increasing) and j's position in each row's support
   std::vector<std::vector<std::pair<int, int>>> rows_of(code->nl);
   for (int r = 0; r < P.m_l; ++r)
@@ -219,6 +233,7 @@ int compile_one(lead_code* code, int side, int prec, std::string* log_out) {
   hs.bp_spb = g.spb;
   hs.bp_cluster = g.cluster;
   hs.bp_smem[prec] = g.smem;
+  hs.bp_maxreg[prec] = maxreg;
   return LEAD_OK;
 }
 
@@ -307,7 +322,187 @@ int jit_launch_bp(const lead_code* code, int side, int prec, const BPJitArgs& ar
   return LEAD_OK;
 }
 
+// Autotuning of one side's kernel in one precision mode: the resident CTAs per SM, i.e. the
+// register cap per thread, from what shared memory allows down to at most three fewer. Every
+// candidate is compiled, loaded and timed (CUDA events, one warm-up and two timed calls of
+// lead_decode) on `shots` shots sampled at p; the fastest is kept for every later call. The
+// geometry (slots, shots per CTA, cluster) and so every output is the same for all candidates.
+int autotune_one(lead_code* code, int side, int prec, double p, int64_t shots, std::string* report) {
+  HostSide& hs = code->side[side];
+  DeviceSide& ds = code->dside[side];
+  int rc = jit_ensure(code, side, prec);            // the default kernel, compiled and loaded
+  if (rc != LEAD_OK) return rc;
+  Geometry g = bp_geometry(code, side, prec);
+  const int top = g.minblocks;
+  const int wm = hs.params.words_m, wn = code->words_n;
+  uint32_t *err = nullptr, *syn = nullptr, *corr = nullptr;
+  uint8_t* st = nullptr;
+  void* ws = nullptr;
+  const size_t wsb = decode_workspace_bytes(code, side);
+  cudaStream_t stream = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(err);
+    cudaFree(syn);
+    cudaFree(corr);
+    cudaFree(st);
+    cudaFree(ws);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (stream) cudaStreamDestroy(stream);
+  };
+  if (cudaMalloc(&err, sizeof(uint32_t) * shots * wn) != cudaSuccess ||
+      cudaMalloc(&syn, sizeof(uint32_t) * shots * wm) != cudaSuccess ||
+      cudaMalloc(&corr, sizeof(uint32_t) * shots * wn) != cudaSuccess || cudaMalloc(&st, shots) != cudaSuccess ||
+      cudaMalloc(&ws, wsb) != cudaSuccess) {
+    cleanup();
+    return LEAD_EOOM;
+  }
+  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cleanup();
+    return LEAD_ECUDA;
+  }
+  rc = lead_sample(code, side == 0 ? LEAD_NOISE_X : LEAD_NOISE_Z, p, shots, 0x5EEDull, 0, side == 0 ? err : nullptr,
+                   side == 0 ? nullptr : err, side == 0 ? syn : nullptr, side == 0 ? nullptr : syn, stream);
+  if (rc != LEAD_OK) {
+    cleanup();
+    return rc;
+  }
+  lead_decode_opts o{};
+  o.side = side;
+  o.use_lead = 1;
+  o.max_iter = 32;
+  o.precision = prec;
+  o.alpha = 1.0f;
+  o.p = p;
+  o.estimator = LEAD_EST_EXACT;
+  auto time_current = [&](float* ms) -> int {
+    int r = lead_decode(code, &o, syn, shots, corr, st, nullptr, nullptr, ws, wsb, stream);     // warm-up
+    if (r != LEAD_OK) return r;
+    if (cudaEventRecord(e0, stream) != cudaSuccess) return LEAD_ECUDA;
+    for (int k = 0; k < 2 && r == LEAD_OK; ++k) r = lead_decode(code, &o, syn, shots, corr, st, nullptr, nullptr, ws, wsb, stream);
+    if (r != LEAD_OK) return r;
+    if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      return LEAD_ECUDA;
+    *ms *= 0.5f;
+    return LEAD_OK;
+  };
+  struct Cand {
+    int minblocks, maxreg, per_sm;
+    long spill;
+    float ms;
+    std::vector<char> cubin;
+    void* lib;
+    void* kern;
+  };
+  std::vector<Cand> cands;
+  // the kernel in use first (compile_one's choice), then every other occupancy
+  {
+    Cand c{};
+    c.minblocks = -1;
+    c.maxreg = hs.bp_maxreg[prec];
+    c.per_sm = ds.bp_per_sm[prec];
+    c.cubin = hs.bp_cubin[prec];
+    c.lib = ds.bp_module[prec];
+    c.kern = ds.bp_func[prec];
+    rc = time_current(&c.ms);
+    if (rc != LEAD_OK) {
+      cleanup();
+      return rc;
+    }
+    cands.push_back(std::move(c));
+  }
+  for (int m = top; m >= std::max(1, top - 3) && rc == LEAD_OK; --m) {
+    Geometry gm = g;
+    gm.minblocks = m;
+    Cand c{};
+    c.minblocks = m;
+    c.maxreg = std::min(255, (65536 / (g.block * m)) & ~7);
+    if (c.maxreg == hs.bp_maxreg[prec]) continue;     // the kernel in use
+    std::string log;
+    rc = nvrtc_build(prelude(code, side, gm, prec) + kLeadJitSource, c.maxreg, &c.cubin, &log);
+    if (rc != LEAD_OK) break;
+    c.spill = spill_bytes(log);
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kern = nullptr;
+    const char* name = hs.bp_cluster > 1 ? "lead_bp_jit_cluster" : "lead_bp_jit";
+    if (cudaLibraryLoadData(&lib, c.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
+        cudaLibraryGetKernel(&kern, lib, name) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs.bp_smem[prec]) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, (const void*)kern, hs.bp_block, hs.bp_smem[prec]) !=
+            cudaSuccess ||
+        c.per_sm < 1) {
+      if (lib) cudaLibraryUnload(lib);
+      rc = LEAD_ECUDA;
+      break;
+    }
+    c.lib = lib;
+    c.kern = kern;
+    // time it in place of the kernel in use
+    void* old_lib = ds.bp_module[prec];
+    void* old_kern = ds.bp_func[prec];
+    const int old_per_sm = ds.bp_per_sm[prec];
+    ds.bp_module[prec] = lib;
+    ds.bp_func[prec] = kern;
+    ds.bp_per_sm[prec] = c.per_sm;
+    rc = time_current(&c.ms);
+    ds.bp_module[prec] = old_lib;
+    ds.bp_func[prec] = old_kern;
+    ds.bp_per_sm[prec] = old_per_sm;
+    cands.push_back(std::move(c));
+  }
+  cleanup();
+  if (rc != LEAD_OK) {
+    for (size_t i = 1; i < cands.size(); ++i) cudaLibraryUnload(static_cast<cudaLibrary_t>(cands[i].lib));
+    return rc;
+  }
+  size_t best = 0;
+  for (size_t i = 1; i < cands.size(); ++i)
+    if (cands[i].ms < cands[best].ms) best = i;
+  std::ostringstream r;
+  r << "side " << side << " precision " << prec << ", " << shots << " shots at p = " << p << ":\n";
+  for (size_t i = 0; i < cands.size(); ++i) {
+    const Cand& c = cands[i];
+    if (c.minblocks < 0) r << "  kernel in use, <= " << c.maxreg << " registers (" << c.per_sm << " resident)";
+    else r << "  " << c.minblocks << " CTA(s) per SM, <= " << c.maxreg << " registers, " << c.spill
+           << " B spilled (" << c.per_sm << " resident)";
+    r << ": " << c.ms << " ms" << (i == best ? "  <- kept" : "") << "\n";
+  }
+  if (report) *report += r.str();
+  // keep the fastest; unload the others (including the kernel in use if it lost)
+  for (size_t i = 0; i < cands.size(); ++i)
+    if (i != best) cudaLibraryUnload(static_cast<cudaLibrary_t>(cands[i].lib));
+  ds.bp_module[prec] = cands[best].lib;
+  ds.bp_func[prec] = cands[best].kern;
+  ds.bp_per_sm[prec] = cands[best].per_sm;
+  hs.bp_cubin[prec] = std::move(cands[best].cubin);
+  hs.bp_maxreg[prec] = cands[best].maxreg;
+  return LEAD_OK;
+}
+
 }  // namespace lead
+
+extern "C" int lead_code_autotune(lead_code* code, int32_t side, int32_t precision, double p, int64_t shots,
+                                  char* report, size_t report_bytes) {
+  if (!code || side < 0 || side > 1 || precision < 0 || precision >= lead::kPrecModes || !(p > 0.0 && p < 0.5) ||
+      shots < 1 || shots > (int64_t)1 << 24)
+    return LEAD_EINVAL;
+  if (code->device < 0) return LEAD_ESTATE;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return LEAD_ECUDA;
+  if (cur != code->device) return LEAD_ESTATE;
+  std::string msg;
+  const int rc = lead::autotune_one(code, side, precision, p, shots, &msg);
+  if (report && report_bytes) {
+    const size_t n = std::min(report_bytes - 1, msg.size());
+    std::memcpy(report, msg.data(), n);
+    report[n] = '\0';
+  }
+  return rc;
+}
 
 extern "C" int lead_code_compile(lead_code* code, char* log, size_t log_bytes) {
   if (!code) return LEAD_EINVAL;

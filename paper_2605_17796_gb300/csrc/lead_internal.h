@@ -68,6 +68,7 @@ struct HostSide {
   std::vector<char> bp_cubin[kPrecModes];   // specialised min-sum kernel per mode (NVRTC output)
   int bp_block = 0, bp_spb = 0, bp_cluster = 1;
   size_t bp_smem[kPrecModes] = {};
+  int bp_maxreg[kPrecModes] = {};          // register cap per thread it was compiled with
 };
 
 }  // namespace lead
@@ -101,6 +102,8 @@ struct BPJitArgs;
 struct Geometry {               // launch geometry of the min-sum kernel for one side
   int spb, cluster, ts, block, minblocks;
   size_t smem;
+  bool alias;                   // one shot per CTA: syndromes and correction bits share the
+                                // message arrays (see bp_geometry)
 };
 Geometry bp_geometry(const lead_code* code, int side, int prec = LEAD_PREC_FP32);
 // Cluster launches whose slot addresses fit 13 bits and owner ranks 2 bits use a u16 partner

@@ -157,6 +157,19 @@ __device__ __forceinline__ void row_weights(float* scr, int tid, const float (&w
   for (int x = 0; x < NX; ++x) scr[scr_index<NX>(tid, x)] = l[x];
 }
 
+// Integer costs of the 2^Delta patterns of one row (sum of the costs of its set bits), into the
+// same scratch as row_weights, as int bit patterns: c(x) = c(x without its lowest bit) + W_lowest.
+template <int DELTA>
+__device__ __forceinline__ void row_costs(float* scr, int tid, const int (&W)[DELTA]) {
+  constexpr int NX = 1 << DELTA;
+  int c[NX];
+  c[0] = 0;
+#pragma unroll
+  for (int x = 1; x < NX; ++x) c[x] = c[x & (x - 1)] + W[lowest_bit(x)];
+#pragma unroll
+  for (int x = 0; x < NX; ++x) scr[scr_index<NX>(tid, x)] = __int_as_float(c[x]);
+}
+
 template <int DELTA, int KB, int ML, int NK>
 __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a) {
   using S = TcShape<DELTA, KB, NK>;
@@ -273,24 +286,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
       float R[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        float m = -INFINITY;
+        float m = -INFINITY, lx[CS];
+#pragma unroll
+        for (int t = 0; t < CS; ++t) {
+          lx[t] = scr[scr_index<NX>(tid, xcls_s[f * CS + t])];
+          m = fmaxf(m, lx[t]);
+        }
+        float sum = 0.0f;
+#pragma unroll
+        for (int t = 0; t < CS; ++t) sum += fast_exp2(lx[t] - m);
+        R[f] = m + __log2f(sum);
+      }
+      // least-cost pattern of every class (the class lists patterns in increasing order, so the
+      // first least cost is the least pattern)
+      row_costs<DELTA>(scr, tid, Wc);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
         int cmin = INT_MAX, xmin = 0;
 #pragma unroll
         for (int t = 0; t < CS; ++t) {
           const int x = xcls_s[f * CS + t];
-          m = fmaxf(m, scr[scr_index<NX>(tid, x)]);
-          int c = 0;
-#pragma unroll
-          for (int b = 0; b < DELTA; ++b) c += ((x >> b) & 1) ? Wc[b] : 0;
-          if (c < cmin) {                 // the class lists patterns in increasing order
+          const int c = __float_as_int(scr[scr_index<NX>(tid, x)]);
+          if (c < cmin) {
             cmin = c;
             xmin = x;
           }
         }
-        float sum = 0.0f;
-#pragma unroll
-        for (int t = 0; t < CS; ++t) sum += fast_exp2(scr[scr_index<NX>(tid, xcls_s[f * CS + t])] - m);
-        R[f] = m + __log2f(sum);
         const int g = f ^ (int)fba;
         cost_s[row * S::CSTR + ra * NF + g] = cmin;
         xmin_s[row * S::XSTR + ra * NF + g] = (uint8_t)xmin;
@@ -456,28 +477,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) prior_local_tc_kernel(TcArgs a)
         rz = 1.0f / Z;
       }
       xor_permute<NF>(agg, fba);           // agg[f] = weight of the members whose row ra is in class f
+      // every pattern's share of its class, times the class's weight, in place of its log-weight
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        float m = -INFINITY, ex[CS];
+#pragma unroll
+        for (int t = 0; t < CS; ++t) {
+          ex[t] = scr[scr_index<NX>(tid, xcls_s[f * CS + t])];
+          m = fmaxf(m, ex[t]);
+        }
+        float sum = 0.0f;
+#pragma unroll
+        for (int t = 0; t < CS; ++t) {
+          ex[t] = fast_exp2(ex[t] - m);
+          sum += ex[t];
+        }
+        const float wgt = agg[f] / sum;
+#pragma unroll
+        for (int t = 0; t < CS; ++t) scr[scr_index<NX>(tid, xcls_s[f * CS + t])] = wgt * ex[t];
+      }
+      // q_b (times Z) = the weighted shares of the patterns with bit b set
       float qb[DELTA];
 #pragma unroll
       for (int b = 0; b < DELTA; ++b) qb[b] = 0.0f;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        float m = -INFINITY;
+      for (int x = 1; x < NX; ++x) {
+        const float u = scr[scr_index<NX>(tid, x)];
 #pragma unroll
-        for (int t = 0; t < CS; ++t) m = fmaxf(m, scr[scr_index<NX>(tid, xcls_s[f * CS + t])]);
-        float sum = 0.0f, tb[DELTA];
-#pragma unroll
-        for (int b = 0; b < DELTA; ++b) tb[b] = 0.0f;
-#pragma unroll
-        for (int t = 0; t < CS; ++t) {
-          const int x = xcls_s[f * CS + t];
-          const float e = fast_exp2(scr[scr_index<NX>(tid, x)] - m);
-          sum += e;
-#pragma unroll
-          for (int b = 0; b < DELTA; ++b) tb[b] += ((x >> b) & 1) ? e : 0.0f;
-        }
-        const float wgt = agg[f] / sum;
-#pragma unroll
-        for (int b = 0; b < DELTA; ++b) qb[b] += wgt * tb[b];
+        for (int b = 0; b < DELTA; ++b)
+          if ((x >> b) & 1) qb[b] += u;
       }
       if (active) {
 #pragma unroll

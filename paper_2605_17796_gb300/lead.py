@@ -69,6 +69,8 @@ EXPORTS = {
     "lead_code_get_check_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _c_uint8_p]),
     "lead_code_compile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "lead_code_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "lead_code_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                          ctypes.c_int64, ctypes.c_char_p, ctypes.c_size_t]),
     "lead_code_get_enumerators": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _c_int32_p, _c_int32_p,
                                                  ctypes.POINTER(ctypes.c_uint64)]),
     "lead_free_code": (None, [ctypes.c_void_p]),
@@ -256,6 +258,13 @@ class Code:
         _check("lead_code_prepare", LIB.lead_code_prepare(self._h, device))
         self.info = self._info()
         return self
+
+    def autotune(self, side: int, precision: int = 0, p: float = 0.05, shots: int = 4096) -> str:
+        """Time the min-sum kernel of (side, precision) at several register caps on `shots`
+        sampled shots at p and keep the fastest (outputs are unchanged); returns the timings."""
+        buf = ctypes.create_string_buffer(1 << 12)
+        _check("lead_code_autotune", LIB.lead_code_autotune(self._h, side, precision, p, shots, buf, len(buf)))
+        return buf.value.decode(errors="replace")
 
     def enumerators(self, side: int):
         i = self.info

@@ -28,6 +28,8 @@ def main(argv=None):
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--priors", action="store_true")
     ap.add_argument("--osd", type=int, default=None, help="also time OSD-CS of this order after decode")
+    ap.add_argument("--autotune", type=int, default=0, help="autotune the decode kernel on this many shots first")
+    ap.add_argument("--report", action="store_true", help="print the min-sum kernels' compile report")
     args = ap.parse_args(argv)
 
     import torch
@@ -35,7 +37,12 @@ def main(argv=None):
     from . import lead
 
     inst = workloads.standard(args.code, 0)
-    code = lead.Code.from_instance(inst).prepare(0)
+    code = lead.Code.from_instance(inst)
+    if args.report:
+        print(code.compile())
+    code.prepare(0)
+    if args.autotune:
+        print(code.autotune(0, args.precision, args.p, args.autotune))
     info = code.info
     shots = args.shots
     ex = torch.zeros((shots, info.words_n), dtype=torch.int32, device="cuda")

