@@ -26,6 +26,8 @@ sys.path.insert(0, ROOT)
 
 P_SWEEP = [round(0.01 * i, 2) for i in range(1, 11)]
 WORKLOAD = "PSL(2,7)"
+PSL11_P = 0.0267          # X marginal 2p/3 of depolarizing p = 0.04, as in the multi-code batch
+TUNE_P = (0.02, 0.03, 0.05)   # priors the min-sum kernel's launch shape is tuned at
 METRIC = "shots decoded/s at matched logical error rate; p50/p99 decode latency (µs)"
 UNIT = "shots/s"
 
@@ -309,13 +311,23 @@ def _local_estimation(lead, code, pipe, hbm_peak: float, shots: int):
     return out
 
 
-def _precision_modes(lead, pipe, shots: int, p: float = 0.05):
+def _kept(report: str) -> str:
+    """The candidate lead_code_autotune kept, from its report."""
+    for line in report.splitlines():
+        if "<- kept" in line:
+            return line.replace("<- kept", "").strip()
+    return ""
+
+
+def _precision_modes(lead, pipe, shots: int, p: float = 0.05, tune_shots: int = 65536):
     """Decode throughput and logical error rate (Wilson 95 % interval) of each storage mode on
-    the same shots at one p."""
+    the same shots at one p. Each mode's min-sum kernel is first autotuned (lead_code_autotune:
+    its register cap chosen by timing, outputs unchanged) on sampled shots at the same p."""
     import torch
     out = {}
     for name, prec in MODES.items():
-        pipe.run(lead.NOISE_X, p, min(shots, pipe.chunk), seed=5, offset=0, precision=prec)   # loads the kernel
+        kept = _kept(pipe.code.autotune(0, prec, p, tune_shots))
+        pipe.run(lead.NOISE_X, p, min(shots, pipe.chunk), seed=5, offset=0, precision=prec)   # warm-up
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -325,8 +337,28 @@ def _precision_modes(lead, pipe, shots: int, p: float = 0.05):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         out[name] = {"shots_per_s": shots / (ms / 1e3), "ler": r.failures / shots,
-                     "ler_ci95": wilson95(r.failures, shots), "mean_iters": r.iters_sum / shots}
+                     "ler_ci95": wilson95(r.failures, shots), "mean_iters": r.iters_sum / shots,
+                     "kernel": kept}
     return out
+
+
+def _batch(lead, dev, scale: float = 0.1, reps: int = 1):
+    """The multi-code batch (SL(2,3) / PSL(2,7) / PSL(2,11) with 10^4 / 2x10^5 / 10^6 shots times
+    `scale`, depolarizing p = 0.04, both sides): eager on one stream with the default kernels,
+    then kernels and plan autotuned and the batch replayed as one CUDA graph."""
+    import workloads
+    from paper_2605_17796_gb300 import batch as mb
+    names = ("SL(2,3)", "PSL(2,7)", "PSL(2,11)")
+    codes = [lead.Code.from_instance(workloads.standard(n, 0)).prepare(dev) for n in names]
+    entries = [mb.Entry(codes[0], int(1e4 * scale), seed=1), mb.Entry(codes[1], int(2e5 * scale), seed=2),
+               mb.Entry(codes[2], int(1e6 * scale), seed=3)]
+    eager_ms, eager_summary = mb.eager_run(entries, reps)
+    best, timings = mb.autotune(entries, reps=reps)
+    ms = best.time_replays(reps)
+    rep = mb.run_report(names, entries, best, timings, ms, eager_ms, eager_summary, reps)
+    rep["scale"] = scale
+    del best
+    return rep
 
 
 def _iterated_lead(lead, pipe, shots: int, ps=(0.02, 0.03), rounds=(1, 2, 3)):
@@ -374,6 +406,8 @@ def main():
     ap.add_argument("--precision-shots", type=int, default=1_000_000)
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--iterated-shots", type=int, default=1 << 18)
+    ap.add_argument("--batch-scale", type=float, default=0.1)
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
 
     if args.oracle_child:
@@ -454,6 +488,9 @@ def main():
             out.append(pipe.run(lead.NOISE_X, p, args.shots_per_p, seed=0, offset=off))
         return out
 
+    # the binary32 kernel's launch shape, chosen by timing at three priors of the sweep; each p
+    # of the sweep uses the shape tuned nearest to it (outputs do not depend on it)
+    tuned = {f"{tp:.2f}": _kept(code.autotune(0, lead.PREC_FP32, tp, 65536)) for tp in TUNE_P}
     for w in range(args.warmup):
         step(10_000 + w)
     torch.cuda.synchronize()
@@ -580,16 +617,25 @@ def main():
     if not args.no_minsum and world == 1:
         minsum = _minsum_baseline(lead, pipe, sink, args.minsum_shots_per_p)
 
-    local_est = precision = iterated = prior_local = None
+    local_est = precision = precision11 = iterated = prior_local = None
     if not args.no_modes and world == 1:
         local_est = _local_estimation(lead, code, pipe, peaks["hbm_gbs"], min(args.chunk, 1 << 20))
         prior_local = _prior_local(lead, code, peaks.get("bf16_tflops", 1900.0))
         precision = _precision_modes(lead, pipe, args.precision_shots)
+        import workloads
+        code11 = lead.Code.from_instance(workloads.standard("PSL(2,11)", 0)).prepare(dev)
+        pipe11 = Pipeline(code11, 1 << 15, dev)
+        precision11 = _precision_modes(lead, pipe11, 1 << 16, p=PSL11_P, tune_shots=8192)
+        del pipe11, code11
         iterated = _iterated_lead(lead, pipe, min(args.iterated_shots, args.chunk))
 
     serving = None
     if not args.no_serving and world == 1:
         serving = _serving(lead, args.serving_rates, args.serving_requests, code)
+
+    batch = None
+    if not args.no_batch and world == 1:
+        batch = _batch(lead, dev, args.batch_scale)
 
     clocks = _clock_summary(clk_path, dev)
     ler = {f"{p:.2f}": f / n for p, f, n in zip(P_SWEEP, sweep_fail, sweep_shots)}
@@ -601,15 +647,18 @@ def main():
                        "shots_per_step": len(P_SWEEP) * args.shots_per_p * world, "max_iter": 32,
                        "alpha": 1.0, "decoder": "LEAD (exact local estimation + merge + min-sum)",
                        "l2": "inputs larger than L2 (2^20-shot chunks, 400 MB of errors)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "min_sum_kernel_by_tuning_p": tuned},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "minsum_baseline": minsum,
             "local_estimation": local_est, "prior_local": prior_local,
             "precision_modes": ({"p": 0.05, "shots": args.precision_shots, "modes": precision}
                                 if precision else None),
+            "precision_modes_psl11": ({"code": "PSL(2,11) (n=11880)", "p": PSL11_P, "shots": 1 << 16,
+                                       "modes": precision11} if precision11 else None),
             "iterated_lead": ({"shots": min(args.iterated_shots, args.chunk), "runs": iterated}
                               if iterated else None),
             "serving": serving,
+            "batch": batch,
             "clocks": clocks, "ler": ler,
             "mean_iters": {f"{p:.2f}": i / n for p, i, n in zip(P_SWEEP, sweep_iters, sweep_shots)}}
     print(json.dumps(line))

@@ -160,23 +160,28 @@ int lead_code_get_check_matrix(const lead_code* code, int32_t side, uint8_t* H);
 int lead_code_compile(lead_code* code, char* log, size_t log_bytes);
 
 /*
- * lead_code_autotune -- choose, by measurement, the resident CTAs per SM of one side's global
- * min-sum kernel (Algorithm 1, Phase 3) in one precision mode. The paper has no counterpart: it
- * is a property of this kernel, whose register cap per thread trades against how many CTAs
- * share an SM. The kernel in use and up to four register caps (what shared memory allows and
- * the three occupancies below it) are compiled, loaded and each timed with CUDA events (one
- * warm-up and two timed lead_decode calls, Phases 1-3, exact estimator, alpha = 1, 32
- * iterations) on `shots` syndromes drawn by lead_sample at p (seed 0x5EED); the fastest is kept
- * for every later call on this code. Only the register allocation differs between candidates:
- * the shots per CTA, the cluster and the arithmetic are the same, so every decode output is
- * bit-identical whichever kernel is kept.
+ * lead_code_autotune -- choose, by measurement, the launch shape of one side's global min-sum
+ * kernel (Algorithm 1, Phase 3) in one precision mode. The paper has no counterpart: these are
+ * properties of this kernel. Candidates: for codes whose shot fits one CTA, one to four times
+ * the default shots per CTA; for codes whose shot is split over a thread-block cluster, clusters
+ * of 2, 3, 4 and 7 CTAs (where the block stays <= 1024 threads and shared memory fits); for
+ * each, the resident CTAs per SM from what shared memory allows down to two fewer (the register
+ * cap per thread trades against them). Each candidate is compiled, loaded and timed with CUDA
+ * events (one warm-up and two timed lead_decode calls, Phases 1-3, exact
+ * estimator, alpha = 1, 32 iterations) on `shots` syndromes drawn by lead_sample at p (seed
+ * 0x5EED). The fastest is kept for later calls on this side and mode whose prior p is nearest
+ * (on a log scale) to this p among the tuned ones: the shape that wins depends on how many
+ * iterations the shots take and how unevenly (several shots per CTA wait for the slowest).
+ * Tuning again at the same p replaces that entry; untuned codes use the default kernel. Every
+ * candidate runs the same arithmetic on every shot, so every decode output is bit-identical
+ * whichever is used.
  *  side, precision  the kernel to tune; p in (0, 1/2); 1 <= shots <= 2^24.
- *  report (host, nullable) receives one line per candidate (cap, spill, resident CTAs, ms),
- *  truncated to report_bytes.
+ *  report (host, nullable) receives one line per candidate (shots per CTA, threads, register
+ *  cap, spilled bytes, resident CTAs, ms), truncated to report_bytes.
  * Allocates and frees its own device buffers and a stream; synchronises with the device. The
  * code must be prepared on the current device, and no other call may use the code meanwhile.
  * Errors: LEAD_EINVAL, LEAD_ESTATE (not prepared on the current device), LEAD_EOOM,
- * LEAD_ECUDA (compilation, loading or a launch failed; the kernel in use is then kept).
+ * LEAD_ECUDA (compilation, loading or a launch failed; the tuned shapes are then unchanged).
  */
 int lead_code_autotune(lead_code* code, int32_t side, int32_t precision, double p, int64_t shots,
                        char* report, size_t report_bytes);

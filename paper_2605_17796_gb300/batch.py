@@ -4,8 +4,10 @@ Each entry (code, shots, noise, p, seed) runs the full pipeline -- sample, decod
 noise touches, check -- on its own stream (or a stream the plan assigns), split into chunks; the
 streams fork from and join back to the capturing stream, so their kernels overlap on the
 device. The whole batch is captured once into a CUDA graph and replayed with one launch.
-A plan (stream of every entry, chunks per entry) is chosen by `autotune`, which captures each
-candidate plan and keeps the one with the shortest replay.
+`autotune` first tunes the min-sum kernel of every code and side the batch decodes
+(`lead_code_autotune`: shots per CTA or cluster size, and register cap, timed on sampled shots;
+outputs do not depend on it), then chooses a plan (stream of every entry, chunks per entry) by
+capturing each candidate plan and keeping the one with the shortest replay.
 """
 from __future__ import annotations
 
@@ -133,8 +135,35 @@ def candidate_plans(n_entries: int, heavy: int):
     return plans
 
 
-def autotune(entries, reps: int = 2, **kw):
-    """Capture every candidate plan and return (best batch, [(plan, ms)])."""
+def _kept(report: str) -> str:
+    for line in report.splitlines():
+        if "<- kept" in line:
+            return line.replace("<- kept", "").strip()
+    return ""
+
+
+def tune_kernels(entries, tune_shots: int = 16384):
+    """Tune the min-sum kernel's launch shape of every (code, side) the entries decode, at the
+    entry's per-side prior, on up to tune_shots sampled shots. Returns {(code index, side): the
+    kept candidate's line of the autotuner's report}. Each code keeps its tuned kernels for every
+    later call."""
+    kept = {}
+    codes = []
+    for e in entries:
+        if all(c is not e.code for c in codes):
+            codes.append(e.code)
+        ci = next(i for i, c in enumerate(codes) if c is e.code)
+        p_side = e.p if e.noise != lead.NOISE_DEPOL else 2.0 * e.p / 3.0
+        for s in MultiCodeBatch.sides(e.noise):
+            if (ci, s) not in kept:
+                kept[(ci, s)] = _kept(e.code.autotune(s, lead.PREC_FP32, p_side, max(256, min(tune_shots, e.shots))))
+    return kept
+
+
+def autotune(entries, reps: int = 2, tune_kernels_first: bool = True, **kw):
+    """Tune the kernels (tune_kernels), then capture every candidate plan; returns (best batch,
+    [(plan, ms)]). The best batch's `kernel_shapes` holds the kernels kept per (code, side)."""
+    shapes = tune_kernels(entries) if tune_kernels_first else {}
     work = [e.shots * e.code.info.n for e in entries]
     heavy = max(range(len(entries)), key=lambda i: work[i])
     best, timings = None, []
@@ -147,14 +176,16 @@ def autotune(entries, reps: int = 2, **kw):
         else:
             del b
         torch.cuda.empty_cache()
+    best[0].kernel_shapes = shapes
     return best[0], timings
 
 
 def main(argv=None):
     """The uneven three-code batch: SL(2,3) / PSL(2,7) / PSL(2,11) with 10^4 / 2x10^5 / 10^6 shots
-    (times --scale), depolarizing p = 0.04. Prints one JSON object: the autotuned plan and its
-    replay time, every candidate's replay time, and the same work issued eagerly on one stream,
-    code after code."""
+    (times --scale), depolarizing p = 0.04. Prints one JSON object: the same work issued eagerly
+    on one stream, code after code, with the library's default kernels; the autotuned kernels
+    and plan and the replay time of its graph; the eager run again with the tuned kernels; and
+    every candidate plan's replay time."""
     import argparse
     import json
 
@@ -168,30 +199,46 @@ def main(argv=None):
     codes = [lead.Code.from_instance(workloads.standard(n, 0)).prepare(0) for n in names]
     entries = [Entry(codes[0], int(1e4 * args.scale), seed=1), Entry(codes[1], int(2e5 * args.scale), seed=2),
                Entry(codes[2], int(1e6 * args.scale), seed=3)]
-    total = sum(e.shots for e in entries)
-    # eager baseline: one stream, one chunk per entry, no graph
+    # eager baseline: one stream, one chunk per entry, no graph, the library's default kernels
+    eager_ms, eager_summary = eager_run(entries, args.reps)
+    best, timings = autotune(entries, reps=args.reps)
+    ms = best.time_replays(args.reps)
+    print(json.dumps(run_report(names, entries, best, timings, ms, eager_ms, eager_summary, args.reps)))
+
+
+def eager_run(entries, reps: int):
+    """Mean time of the batch issued eagerly on one stream, one chunk per entry, and its summary."""
     eager = MultiCodeBatch(entries, plan=[(0, 1)] * len(entries))
     eager.issue()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.reps):
+    for _ in range(reps):
         eager.issue()
     e1.record()
     torch.cuda.synchronize()
-    eager_ms = e0.elapsed_time(e1) / args.reps
-    eager_summary = eager.summary()
+    ms = e0.elapsed_time(e1) / reps
+    summary = eager.summary()
     del eager
     torch.cuda.empty_cache()
-    best, timings = autotune(entries, reps=args.reps)
-    ms = best.time_replays(args.reps)
-    print(json.dumps({"entries": [{"code": n, "shots": e.shots} for n, e in zip(names, entries)],
-                      "noise": "depolarizing p=0.04, both sides", "plan": best.plan, "replay_ms": ms,
-                      "shots_per_s": total / ms * 1e3, "eager_one_stream_ms": eager_ms,
-                      "eager_shots_per_s": total / eager_ms * 1e3,
-                      "candidates": [{"plan": p, "ms": t} for p, t in timings],
-                      "summary": best.summary(), "eager_summary": eager_summary}))
+    return ms, summary
+
+
+def run_report(names, entries, best, timings, ms, eager_ms, eager_summary, reps: int) -> dict:
+    total = sum(e.shots for e in entries)
+    tuned_eager_ms, _ = eager_run(entries, reps)
+    summary = best.summary()
+    return {"entries": [{"code": n, "shots": e.shots} for n, e in zip(names, entries)],
+            "noise": "depolarizing p=0.04, both sides", "plan": best.plan,
+            "kernel_shapes": {f"{names[ci]} side {s}": k for (ci, s), k in best.kernel_shapes.items()},
+            "replay_ms": ms, "shots_per_s": total / ms * 1e3,
+            "eager_default_kernels_ms": eager_ms, "eager_default_shots_per_s": total / eager_ms * 1e3,
+            "speedup_vs_eager_default": eager_ms / ms,
+            "eager_tuned_kernels_ms": tuned_eager_ms, "speedup_of_graph_plan": tuned_eager_ms / ms,
+            "candidates": [{"plan": p, "ms": t} for p, t in timings],
+            "failures_equal_to_eager": [a["failures"] == b["failures"] for a, b in zip(summary, eager_summary)],
+            "summary": summary}
 
 
 if __name__ == "__main__":

@@ -3,9 +3,10 @@
 //   LEAD_NL (Delta^2), LEAD_ML (local rows m_l), LEAD_TS (threads with work = shots per CTA *
 //   |G|), LEAD_BLOCK (block size), LEAD_MINBLOCKS (CTAs per SM), LEAD_KMAX, LEAD_JMAX,
 //   LEAD_PREC (storage format), and the constant tables lead_jit::kLen[ML] (row weights),
-//   kSupp[ML][KMAX] (local indices of every local row, increasing), kRowMask[ML] (the same rows
-//   as 64-bit masks) and, per slot j, kJLen[NL], kJRow[NL][JMAX], kJPos[NL][JMAX] (the local
-//   rows touching j in increasing order and j's position in each row's support),
+//   kSupp[ML][KMAX] (local indices of every local row, increasing), kRowLo[ML] / kRowHi[ML]
+//   (the same rows as masks over the two hard-decision words) and, per slot j, kJLen[NL],
+//   kJRow[NL][JMAX], kJPos[NL][JMAX] (the local rows touching j in increasing order and j's
+//   position in each row's support),
 // so every loop over a check's support below has compile-time trip counts and offsets.
 //
 // Mapping: one CTA handles `spb` shots; thread t = shot sl * |G| + vertex v. Shared memory is
@@ -100,7 +101,7 @@ struct RowMag {
 };
 
 // Shared-memory offset (bytes) of the word arrays behind the three NL x TS message arrays.
-constexpr unsigned int kMsgBytes = ((3u * LEAD_NL * LEAD_TS * (unsigned int)sizeof(msg_t)) + 15u) & ~15u;
+[[maybe_unused]] constexpr unsigned int kMsgBytes = ((3u * LEAD_NL * LEAD_TS * (unsigned int)sizeof(msg_t)) + 15u) & ~15u;
 
 // Phases 1-2 for one slot: the merged prior LLR of the table entries e0 (this view) and e1 (the
 // partner view), lambda(alpha * ((q(e0) + q(e1)) * 1/2)). With K > 0 classes it is one lookup in
@@ -122,11 +123,80 @@ __device__ __forceinline__ float c2v_msg(float m1, float m2, unsigned int meta, 
   const float mag = (k == (int)((meta >> 26) & 31u)) ? m2 : m1;
   return __uint_as_float(__float_as_uint(mag) ^ (((flip >> (len - 1 - k)) & 1u) << 31));
 }
+
+// Check-node update of the thread's ML local rows (sv: their syndrome bits) from the posteriors
+// of its own slots in P: every v2c = post - c2v_old, then the row's new (min1, min2, meta).
+__device__ __forceinline__ void check_update(RowMag (&mag)[LEAD_ML], unsigned int (&meta)[LEAD_ML], unsigned int sv,
+                                             const msg_t* P, int tid) {
+#pragma unroll
+  for (int r = 0; r < LEAD_ML; ++r) {
+    const float m1o = mag[r].m1(), m2o = mag[r].m2();
+    const unsigned int mo = meta[r];
+    const int amo = (int)((mo >> 26) & 31u);
+    const unsigned int flip = mo ^ (0u - (mo >> 31));   // bit len-1-k: sign of the old message to k
+    float n1 = __int_as_float(0x7F800000), n2 = __int_as_float(0x7F800000);
+    int am = 0;
+    unsigned int sg = 0;
+#pragma unroll
+    for (int k = 0; k < LEAD_KMAX; ++k) {
+      if (k >= kLen[r]) break;      // constant after unrolling
+      const float mago = (k == amo) ? m2o : m1o;
+      const float co = __uint_as_float(__float_as_uint(mago) ^ ((flip >> (kLen[r] - 1 - k)) << 31));
+      const float v2c = __fsub_rn(dec(P[kSupp[r][k] * LEAD_TS + tid]), co);
+      const float m = fabsf(v2c);
+      // v2c is never -0 (every sum starts from +0 terms): its sign bit equals v2c < 0
+      sg = __funnelshift_l(__float_as_uint(v2c), sg, 1);
+      const bool lt = m < n1;
+      n2 = lt ? n1 : fminf(n2, m);
+      n1 = lt ? m : n1;
+      am = lt ? k : am;
+    }
+    const unsigned int par = ((unsigned int)__popc(sg) ^ (sv >> r)) & 1u;
+    mag[r].set(n1, n2);
+    meta[r] = sg | ((unsigned int)am << 26) | (par << 31);
+  }
+}
+
+// U of every slot from the rows' new states: the messages of the rows touching the slot summed
+// in increasing row order (binary32, the first term stored as is: 0 + c == c), stored once into
+// U (own slots).
+__device__ __forceinline__ void store_u(const RowMag (&mag)[LEAD_ML], const unsigned int (&meta)[LEAD_ML], msg_t* U,
+                                        int tid) {
+#pragma unroll
+  for (int j = 0; j < LEAD_NL; ++j) {
+    float u = 0.0f;
+#pragma unroll
+    for (int i = 0; i < LEAD_JMAX; ++i) {
+      if (i >= kJLen[j]) break;     // constant after unrolling
+      const int r = kJRow[j][i];
+      const float c = c2v_msg(mag[r].m1(), mag[r].m2(), meta[r], kJPos[j][i], kLen[r]);
+      u = (i == 0) ? c : __fadd_rn(u, c);
+    }
+    U[j * LEAD_TS + tid] = enc(u);
+  }
+}
+
+// Posterior of slot j from the prior lj, this view's sum uo and the partner view's sum up, in
+// the qubit's order (lambda + U_first) + U_second.
+__device__ __forceinline__ float slot_post(bool first, float lj, float uo, float up) {
+  return first ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo);
+}
 }  // namespace lead_jit
 
 #if LEAD_CLUSTER == 1
 namespace lead_jit {
 
+// Iteration schedule. With one shot per CTA (LEAD_SPB == 1) an iteration has one barrier: the
+// first two message arrays, X and Y, trade roles every iteration. Phase A reads the sums U of the previous
+// iteration from X (own and partner slots) and writes the posteriors into Y; the check update
+// reads the thread's own posteriors from Y and then overwrites them with the new sums U; the
+// barrier (which also gathers the local check failures into the shot's verdict) orders those
+// writes before the partners' reads in the next iteration, whose posteriors go into X. The
+// verdict of iteration t is therefore known after its check update, which a converged shot
+// computes once in vain; the outputs are the posteriors of iteration t, recomputed from X.
+// With several shots per CTA each shot has its own verdict, and the iteration keeps two
+// barriers (timed faster than one barrier with every thread reading every shot's verdict);
+// a shot that has stopped leaves its threads idle until the batch is done.
 extern "C" __global__ void __launch_bounds__(LEAD_BLOCK, LEAD_MINBLOCKS)
 lead_bp_jit(const lead::BPJitArgs a) {
   constexpr int NL = LEAD_NL, ML = LEAD_ML, TS = LEAD_TS;
@@ -137,15 +207,14 @@ lead_bp_jit(const lead::BPJitArgs a) {
   msg_t* Ls = Ps + NL * TS;
 #if LEAD_ALIAS
   // one shot per CTA: the staged syndromes live in the posterior array (read by the prologue
-  // only, before the first iteration writes posteriors) and the correction bits in the prior
-  // array (dead once the shot has stopped)
+  // only, before the first iteration writes posteriors) and the correction bits in the array
+  // whose sums U are dead when the shot stops
   unsigned int* syn_s = reinterpret_cast<unsigned int*>(Ps);
-  unsigned int* cb = reinterpret_cast<unsigned int*>(Ls);
-  int* flags = nullptr;
 #else
   unsigned int* syn_s = smem + kMsgBytes / 4;
   unsigned int* cb = syn_s + spb * wm;
-  int* flags = reinterpret_cast<int*>(cb + spb * a.words_n);
+  int* flags = reinterpret_cast<int*>(cb + spb * a.words_n);     // per-shot verdicts (several shots)
+  (void)flags;
 #endif
   const unsigned short* __restrict__ PA = a.pa;
 
@@ -158,7 +227,7 @@ lead_bp_jit(const lead::BPJitArgs a) {
   for (long long g0 = (long long)blockIdx.x * spb; g0 < a.shots; g0 += (long long)gridDim.x * spb) {
     const int nsh = (int)((a.shots - g0) < spb ? (a.shots - g0) : spb);
     for (int i = tid; i < nsh * wm; i += blockDim.x) syn_s[i] = __ldg(a.syn + g0 * wm + i);
-#if !LEAD_ALIAS
+#if LEAD_SPB > 1
     for (int i = tid; i < spb * a.words_n; i += blockDim.x) cb[i] = 0u;
     if (tid < 2 * spb) flags[tid] = 0;
 #endif
@@ -195,6 +264,70 @@ lead_bp_jit(const lead::BPJitArgs a) {
       }
     }
     __syncthreads();
+#if LEAD_SPB == 1
+    msg_t* X = Us;      // sums U of the previous iteration
+    msg_t* Y = Ps;      // this iteration's posteriors, then its sums U
+    for (int t = 0;; ++t) {
+      HardBits hm;
+      unsigned int bad = 0;
+      if (act) {
+#pragma unroll
+        for (int j = 0; j < NL; ++j) {
+          const unsigned int pa = __ldg(PA + j * TS + tid);
+          const float up = lead::in_bounds(a.check, pa & 0x7FFFu, NL * TS, 1) ? dec(X[pa & 0x7FFFu]) : 0.0f;
+          const msg_t pe = enc(slot_post(pa >> 15, dec(Ls[j * TS + tid]), dec(X[j * TS + tid]), up));
+          Y[j * TS + tid] = pe;
+          hm.push_neg(j, dec(pe));
+        }
+#pragma unroll
+        for (int r = 0; r < ML; ++r) bad |= (hm.row_parity(r) ^ (sv >> r)) & 1u;
+      }
+      const bool last = t >= a.max_iter;      // uniform
+      if (act && !last) {
+        check_update(mag, meta, sv, Y, tid);
+        store_u(mag, meta, Y, tid);
+      }
+      // the block-wide OR of the local check failures is the shot's verdict
+      const bool conv = !__syncthreads_or(bad);
+      if (conv || last) {                      // uniform across the CTA
+#if LEAD_ALIAS
+        unsigned int* cbw = reinterpret_cast<unsigned int*>(Y);
+#else
+        unsigned int* cbw = cb;
+#endif
+        for (int i = tid; i < a.words_n; i += blockDim.x) cbw[i] = 0u;
+        __syncthreads();
+        if (act) {
+          for (int j = 0; j < NL; ++j) {
+            const unsigned int pa = __ldg(PA + j * TS + tid);
+            if (pa >> 15) {
+              const int q = __ldg(a.views + v * NL + j);
+              if (!lead::in_bounds(a.check, q, a.n, 3)) continue;
+              if (hm.get(j)) atomicOr(cbw + (q >> 5), 1u << (q & 31));
+              if (a.llr) {
+                // the posterior of iteration t again, from the same stored operands
+                const float up = lead::in_bounds(a.check, pa & 0x7FFFu, NL * TS, 1) ? dec(X[pa & 0x7FFFu]) : 0.0f;
+                a.llr[g0 * a.n + q] = rnd(slot_post(true, dec(Ls[j * TS + tid]), dec(X[j * TS + tid]), up));
+              }
+            }
+          }
+          if (v == 0) {
+            a.status[g0] = conv ? (unsigned char)1 : (unsigned char)2;
+            if (a.iters) a.iters[g0] = t;
+          }
+        }
+        __syncthreads();     // every thread's correction bits are in cbw before the copy-out
+        for (int i = tid; i < a.words_n; i += blockDim.x) a.corr[g0 * a.words_n + i] = cbw[i];
+        __syncthreads();     // the copy-out has read cbw before the next shot stages its syndromes
+        break;
+      }
+      msg_t* const T = X;
+      X = Y;
+      Y = T;
+    }
+#else
+    // several shots per CTA, each with its own verdict: two barriers per iteration (the verdicts
+    // of all shots are read between them, so every thread leaves the loop at the same iteration)
     bool mydone = !act;
     for (int t = 0;; ++t) {
       HardBits hm;
@@ -204,31 +337,17 @@ lead_bp_jit(const lead::BPJitArgs a) {
         for (int j = 0; j < NL; ++j) {
           const unsigned int pa = __ldg(PA + j * TS + tid);
           const float up = lead::in_bounds(a.check, pa & 0x7FFFu, NL * TS, 1) ? dec(Us[pa & 0x7FFFu]) : 0.0f;
-          const float uo = dec(Us[j * TS + tid]);
-          const float lj = dec(Ls[j * TS + tid]);
-          const msg_t pe = enc((pa >> 15) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo));
+          const msg_t pe = enc(slot_post(pa >> 15, dec(Ls[j * TS + tid]), dec(Us[j * TS + tid]), up));
           Ps[j * TS + tid] = pe;
           hm.push_neg(j, dec(pe));
         }
 #pragma unroll
         for (int r = 0; r < ML; ++r) bad |= (hm.row_parity(r) ^ (sv >> r)) & 1u;
       }
-      bool conv;
-      if (LEAD_SPB == 1) {
-        // one shot per CTA: the block-wide OR of the local check failures is the shot's verdict
-        conv = !__syncthreads_or(bad);
-      } else {
-        if (bad) atomicOr(flags + (t & 1) * spb + sl, 1);
-        if (tid < spb) flags[((t + 1) & 1) * spb + tid] = 0;
-        __syncthreads();
-        conv = flags[(t & 1) * spb + sl] == 0;
-      }
-#if LEAD_ALIAS
-      if (conv || t >= a.max_iter) {      // uniform: the prior array now takes the correction bits
-        for (int i = tid; i < a.words_n; i += blockDim.x) cb[i] = 0u;
-        __syncthreads();
-      }
-#endif
+      if (bad) atomicOr(flags + (t & 1) * spb + sl, 1);
+      if (tid < spb) flags[((t + 1) & 1) * spb + tid] = 0;
+      __syncthreads();
+      const bool conv = flags[(t & 1) * spb + sl] == 0;
       if (!mydone && (conv || t >= a.max_iter)) {
         const long long shot = g0 + sl;
         for (int j = 0; j < NL; ++j) {
@@ -245,59 +364,17 @@ lead_bp_jit(const lead::BPJitArgs a) {
         }
         mydone = true;
       }
-      if (LEAD_SPB == 1) {
-        if (conv || t >= a.max_iter) break;       // uniform across the CTA
-      } else {
-        if (!__syncthreads_or(!mydone)) break;
-      }
+      if (!__syncthreads_or(!mydone)) break;
       if (!mydone) {
-#pragma unroll
-        for (int r = 0; r < ML; ++r) {
-          const float m1o = mag[r].m1(), m2o = mag[r].m2();
-          const unsigned int mo = meta[r];
-          const int amo = (int)((mo >> 26) & 31u);
-          const unsigned int flip = mo ^ (0u - (mo >> 31));   // bit len-1-k: sign of the old message to k
-          float n1 = __int_as_float(0x7F800000), n2 = __int_as_float(0x7F800000);
-          int am = 0;
-          unsigned int sg = 0;
-#pragma unroll
-          for (int k = 0; k < LEAD_KMAX; ++k) {
-            if (k >= kLen[r]) break;      // constant after unrolling
-            const float mago = (k == amo) ? m2o : m1o;
-            const float co = __uint_as_float(__float_as_uint(mago) ^ ((flip >> (kLen[r] - 1 - k)) << 31));
-            const float v2c = __fsub_rn(dec(Ps[kSupp[r][k] * TS + tid]), co);
-            const float m = fabsf(v2c);
-            // v2c is never -0 (every sum starts from +0 terms): its sign bit equals v2c < 0
-            sg = __funnelshift_l(__float_as_uint(v2c), sg, 1);
-            const bool lt = m < n1;
-            n2 = lt ? n1 : fminf(n2, m);
-            n1 = lt ? m : n1;
-            am = lt ? k : am;
-          }
-          const unsigned int par = ((unsigned int)__popc(sg) ^ (sv >> r)) & 1u;
-          mag[r].set(n1, n2);
-          meta[r] = sg | ((unsigned int)am << 26) | (par << 31);
-        }
-        // U of every slot: its rows' new messages summed in increasing row order (binary32, the
-        // first term stored as is: 0 + c == c), then stored once
-#pragma unroll
-        for (int j = 0; j < NL; ++j) {
-          float u = 0.0f;
-#pragma unroll
-          for (int i = 0; i < LEAD_JMAX; ++i) {
-            if (i >= kJLen[j]) break;     // constant after unrolling
-            const int r = kJRow[j][i];
-            const float c = c2v_msg(mag[r].m1(), mag[r].m2(), meta[r], kJPos[j][i], kLen[r]);
-            u = (i == 0) ? c : __fadd_rn(u, c);
-          }
-          Us[j * TS + tid] = enc(u);
-        }
+        check_update(mag, meta, sv, Ps, tid);
+        store_u(mag, meta, Us, tid);
       }
       __syncthreads();
     }
     __syncthreads();     // every thread's correction bits are in cb before the copy-out
     for (int i = tid; i < nsh * a.words_n; i += blockDim.x) a.corr[g0 * a.words_n + i] = cb[i];
     __syncthreads();
+#endif
   }
 }
 
@@ -309,8 +386,8 @@ lead_bp_jit(const lead::BPJitArgs a) {
 // The same decoder for codes whose per-shot state exceeds one CTA's shared memory: a cluster of
 // LEAD_CLUSTER CTAs handles one shot, CTA rank r owning vertices r*TS .. r*TS + TS - 1 (TS =
 // LEAD_TS). A partner slot owned by another CTA is read from that CTA's shared memory through
-// the cluster's distributed shared memory (mapa to a generic address, then a plain load). The iteration's two
-// synchronisation points are cluster barriers; the shot's verdict is one flag word in rank 0,
+// the cluster's distributed shared memory (mapa to a generic address, then a plain load). The iteration's one
+// synchronisation point is a cluster barrier; the shot's verdict is one flag word in rank 0,
 // OR-ed by every thread with a violated local check and read back by all threads after the
 // barrier, so every CTA of the cluster takes the same branch at every step.
 // The partner table [j][v] (per global vertex v) holds the partner slot's word address inside
@@ -397,22 +474,22 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
   msg_t* Ps = Us + NL * TS;
   msg_t* Ls = Ps + NL * TS;
 #if LEAD_ALIAS
-  // the staged syndromes live in the posterior array and the correction bits in the prior array
-  // (see the single-CTA kernel); the two verdict words follow the messages
+  // the staged syndromes live in the posterior array and the correction bits in the array whose
+  // sums U are dead when the shot stops (see the single-CTA kernel); the three verdict words
+  // follow the messages
   unsigned int* syn_s = reinterpret_cast<unsigned int*>(Ps);
-  unsigned int* cb = reinterpret_cast<unsigned int*>(Ls);
-  unsigned int* flags = smem + kMsgBytes / 4;    // two words, meaningful in rank 0 only
+  unsigned int* flags = smem + kMsgBytes / 4;    // three words, meaningful in rank 0 only
 #else
   unsigned int* syn_s = smem + kMsgBytes / 4;
   unsigned int* cb = syn_s + wm;
-  unsigned int* flags = cb + a.words_n;          // two words, meaningful in rank 0 only
+  unsigned int* flags = cb + a.words_n;          // three words, meaningful in rank 0 only
 #endif
 
   const unsigned int rank = cluster_rank();
   const int tid = threadIdx.x;
   const int v = (int)rank * TS + tid;            // global vertex of this thread
   const bool lane_ok = tid < TS && v < V;
-  const msg_t* ubase[C];          // every rank's U array, as generic addresses
+  const msg_t* ubase[C];          // every rank's first message array, as generic addresses
 #pragma unroll
   for (int r = 0; r < C; ++r) ubase[r] = map_rank_generic(Us, r);
   const unsigned int flag0 = map_rank(flags, 0);
@@ -422,10 +499,7 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
 
   for (long long g0 = cid; g0 < a.shots; g0 += ncl) {
     for (int i = tid; i < wm; i += blockDim.x) syn_s[i] = __ldg(a.syn + g0 * wm + i);
-#if !LEAD_ALIAS
-    for (int i = tid; i < a.words_n; i += blockDim.x) cb[i] = 0u;
-#endif
-    if (tid < 2) flags[tid] = 0u;
+    if (tid < 3) flags[tid] = 0u;
     RowMag mag[ML];
     unsigned int meta[ML];
 #pragma unroll
@@ -459,7 +533,13 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
       }
     }
     cluster_sync();             // zeroed U and cleared flags visible to the whole cluster
+    // One cluster barrier per iteration: the first two message arrays trade roles every
+    // iteration in every CTA alike (X at offset xo, Y at NL*TS - xo), as in the single-CTA kernel.
+    unsigned int fi = 0;        // verdict word of this iteration (three in rotation)
     for (int t = 0;; ++t) {
+      const int xo = (t & 1) ? NL * TS : 0;
+      msg_t* X = Us + xo;
+      msg_t* Y = Us + (NL * TS - xo);
       HardBits hm;
       unsigned int bad = 0;
       if (lane_ok) {
@@ -480,8 +560,9 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
 #pragma unroll
               for (int r = 1; r < C; ++r) ub = (pr == (unsigned int)r) ? ubase[r] : ub;
               // ordered after the previous cluster barrier (memory clobber)
-              upr[g] = (lead::in_bounds(a.check, addr, NL * TS, 1) && lead::in_bounds(a.check, pr, C, 4)) ? ub[addr]
-                                                                                                       : enc(0.0f);
+              upr[g] = (lead::in_bounds(a.check, addr, NL * TS, 1) && lead::in_bounds(a.check, pr, C, 4))
+                           ? ub[xo + addr]
+                           : enc(0.0f);
               first |= (unsigned int)pt.first << g;
             }
           }
@@ -489,67 +570,51 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
           for (int g = 0; g < G; ++g) {
             const int j = j0 + g;
             if (j < NL) {
-              const float up = dec(upr[g]);
-              const float uo = dec(Us[j * TS + tid]);
-              const float lj = dec(Ls[j * TS + tid]);
-              const msg_t pe =
-                  enc(((first >> g) & 1u) ? __fadd_rn(__fadd_rn(lj, uo), up) : __fadd_rn(__fadd_rn(lj, up), uo));
-              Ps[j * TS + tid] = pe;
+              const msg_t pe = enc(slot_post((first >> g) & 1u, dec(Ls[j * TS + tid]), dec(X[j * TS + tid]),
+                                             dec(upr[g])));
+              Y[j * TS + tid] = pe;
               hm.push_neg(j, dec(pe));
             }
           }
         }
 #pragma unroll
         for (int r = 0; r < ML; ++r) bad |= (hm.row_parity(r) ^ (sv >> r)) & 1u;
-        if (bad) red_cluster_or(flag0 + 4u * (t & 1), 1u);
+        if (bad) red_cluster_or(flag0 + 4u * fi, 1u);
       }
-      if (rank == 0 && tid == 0) flags[(t + 1) & 1] = 0u;
-      cluster_arrive();
-      // the check-node update reads only this thread's own posteriors: computed between the
-      // barrier's arrive and its wait, it hides the barrier (discarded if the shot stops here)
-      if (lane_ok && t < a.max_iter) {
-#pragma unroll
-        for (int r = 0; r < ML; ++r) {
-          const float m1o = mag[r].m1(), m2o = mag[r].m2();
-          const unsigned int mo = meta[r];
-          const int amo = (int)((mo >> 26) & 31u);
-          const unsigned int flip = mo ^ (0u - (mo >> 31));
-          float n1 = __int_as_float(0x7F800000), n2 = __int_as_float(0x7F800000);
-          int am = 0;
-          unsigned int sg = 0;
-#pragma unroll
-          for (int k = 0; k < LEAD_KMAX; ++k) {
-            if (k >= kLen[r]) break;
-            const float mago = (k == amo) ? m2o : m1o;
-            const float co = __uint_as_float(__float_as_uint(mago) ^ ((flip >> (kLen[r] - 1 - k)) << 31));
-            const float v2c = __fsub_rn(dec(Ps[kSupp[r][k] * TS + tid]), co);
-            const float m = fabsf(v2c);
-            sg = __funnelshift_l(__float_as_uint(v2c), sg, 1);
-            const bool lt = m < n1;
-            n2 = lt ? n1 : fminf(n2, m);
-            n1 = lt ? m : n1;
-            am = lt ? k : am;
-          }
-          const unsigned int par = ((unsigned int)__popc(sg) ^ (sv >> r)) & 1u;
-          mag[r].set(n1, n2);
-          meta[r] = sg | ((unsigned int)am << 26) | (par << 31);
-        }
+      const unsigned int fn = fi == 2u ? 0u : fi + 1u;
+      if (rank == 0 && tid == 0) flags[fn] = 0u;     // last read two barriers ago
+      const bool last = t >= a.max_iter;            // uniform
+      if (lane_ok && !last) {
+        check_update(mag, meta, sv, Y, tid);
+        store_u(mag, meta, Y, tid);
       }
-      cluster_wait();
-      const bool conv = ld_cluster_u32(flag0 + 4u * (t & 1)) == 0u;
-      if (conv || t >= a.max_iter) {
+      cluster_sync();           // every CTA's U and every verdict bit in place
+      const bool conv = ld_cluster_u32(flag0 + 4u * fi) == 0u;
+      if (conv || last) {       // uniform across the cluster: every thread read the same flag
 #if LEAD_ALIAS
-        // this CTA's priors are dead (its gathers of this iteration are done): correction bits
-        for (int i = tid; i < a.words_n; i += blockDim.x) cb[i] = 0u;
-        __syncthreads();
+        unsigned int* cbw = reinterpret_cast<unsigned int*>(Y);
+#else
+        unsigned int* cbw = cb;
 #endif
+        for (int i = tid; i < a.words_n; i += blockDim.x) cbw[i] = 0u;
+        __syncthreads();
         if (lane_ok) {
           for (int j = 0; j < NL; ++j) {
-            if (cluster_partner(a.pa, j, v, V).first) {
+            const Partner pt = cluster_partner(a.pa, j, v, V);
+            if (pt.first) {
               const int q = __ldg(a.views + v * NL + j);
               if (!lead::in_bounds(a.check, q, a.n, 3)) continue;
-              if (hm.get(j)) atomicOr(cb + (q >> 5), 1u << (q & 31));
-              if (a.llr) a.llr[g0 * a.n + q] = dec(Ps[j * TS + tid]);
+              if (hm.get(j)) atomicOr(cbw + (q >> 5), 1u << (q & 31));
+              if (a.llr) {
+                // the posterior of iteration t again, from the same stored operands (no CTA
+                // writes its X before the barriers below)
+                const msg_t* ub = ubase[0];
+#pragma unroll
+                for (int r = 1; r < C; ++r) ub = (pt.rank == (unsigned int)r) ? ubase[r] : ub;
+                const bool ok = lead::in_bounds(a.check, pt.addr, NL * TS, 1) && lead::in_bounds(a.check, pt.rank, C, 4);
+                const float up = ok ? dec(ub[xo + pt.addr]) : 0.0f;
+                a.llr[g0 * a.n + q] = rnd(slot_post(true, dec(Ls[j * TS + tid]), dec(X[j * TS + tid]), up));
+              }
             }
           }
         }
@@ -557,36 +622,20 @@ lead_bp_jit_cluster(const lead::BPJitArgs a) {
           a.status[g0] = conv ? (unsigned char)1 : (unsigned char)2;
           if (a.iters) a.iters[g0] = t;
         }
-        break;                  // uniform across the cluster: every thread read the same flag
-      }
-      if (lane_ok) {
-        // U of every slot: its rows' new messages summed in increasing row order (binary32, the
-        // first term stored as is: 0 + c == c), then stored once
+        cluster_sync();         // every CTA's correction bits are in its cbw
+        if (rank == 0) {
+          for (int i = tid; i < a.words_n; i += blockDim.x) {
+            unsigned int w = cbw[i];
 #pragma unroll
-        for (int j = 0; j < NL; ++j) {
-          float u = 0.0f;
-#pragma unroll
-          for (int i = 0; i < LEAD_JMAX; ++i) {
-            if (i >= kJLen[j]) break;     // constant after unrolling
-            const int r = kJRow[j][i];
-            const float c = c2v_msg(mag[r].m1(), mag[r].m2(), meta[r], kJPos[j][i], kLen[r]);
-            u = (i == 0) ? c : __fadd_rn(u, c);
+            for (int r = 1; r < C; ++r) w |= ld_cluster_u32(map_rank(cbw + i, r));
+            a.corr[g0 * a.words_n + i] = w;
           }
-          Us[j * TS + tid] = enc(u);
         }
+        cluster_sync();         // rank 0 has read every cbw and every CTA its partners' X
+        break;
       }
-      cluster_sync();           // every CTA's U complete before the next gather
+      fi = fn;
     }
-    cluster_sync();             // every CTA's correction bits are in its cb
-    if (rank == 0) {
-      for (int i = tid; i < a.words_n; i += blockDim.x) {
-        unsigned int w = cb[i];
-#pragma unroll
-        for (int r = 1; r < C; ++r) w |= ld_cluster_u32(map_rank(cb + i, r));
-        a.corr[g0 * a.words_n + i] = w;
-      }
-    }
-    cluster_sync();             // rank 0 has read every cb before the next shot clears them
   }
 }
 

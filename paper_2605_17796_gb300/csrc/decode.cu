@@ -96,7 +96,7 @@ local_estimate_kernel(LocalArgs a, __grid_constant__ const SideParams P) {
 }  // namespace
 
 int bp_shots_per_block(const lead_code* code) {
-  return std::max(1, 256 / code->order);
+  return std::max(1, std::min(16, 256 / code->order));     // at most 64 after autotuning (x4)
 }
 
 namespace {

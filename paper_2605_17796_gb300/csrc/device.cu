@@ -10,6 +10,53 @@
 
 namespace lead {
 
+std::vector<uint16_t> single_cta_partner_table(const lead_code* code, int side, const Geometry& g) {
+  const HostSide& hs = code->side[side];
+  const int nl = code->nl;
+  std::vector<uint16_t> pa((size_t)nl * g.ts, 0);
+  for (int sl = 0; sl < g.spb; ++sl)
+    for (int v = 0; v < code->order; ++v)
+      for (int j = 0; j < nl; ++j) {
+        const uint32_t raw = hs.partner[(size_t)v * nl + j];
+        const uint32_t ps = raw & 0x7FFFFFFFu;
+        const uint32_t vp = ps / nl, jp = ps % nl;
+        const int t = sl * code->order + v;
+        pa[(size_t)j * g.ts + t] = (uint16_t)((jp * g.ts + sl * code->order + vp) | ((raw >> 31) << 15));
+      }
+  return pa;
+}
+
+std::vector<uint8_t> partner_table_bytes(const lead_code* code, int side, const Geometry& g) {
+  const HostSide& hs = code->side[side];
+  const int nl = code->nl;
+  std::vector<uint8_t> out;
+  auto as_bytes = [&](const auto& v) {
+    out.resize(v.size() * sizeof(v[0]));
+    std::memcpy(out.data(), v.data(), out.size());
+  };
+  if (g.cluster == 1) {
+    if ((size_t)nl * g.ts < 32768) as_bytes(single_cta_partner_table(code, side, g));
+    return out;
+  }
+  const bool pa16 = cluster_pa16(g, nl);
+  std::vector<uint16_t> p16(pa16 ? (size_t)nl * code->order : 0, 0);
+  std::vector<uint32_t> p32(pa16 ? 0 : (size_t)nl * code->order, 0);
+  for (int v = 0; v < code->order; ++v)
+    for (int j = 0; j < nl; ++j) {
+      const uint32_t raw = hs.partner[(size_t)v * nl + j];
+      const uint32_t ps = raw & 0x7FFFFFFFu;
+      const uint32_t vp = ps / nl, jp = ps % nl;
+      const uint32_t owner = vp / g.ts, tp = vp - owner * g.ts;
+      if (pa16) p16[(size_t)j * code->order + v] = (uint16_t)((jp * g.ts + tp) | (owner << 13) | ((raw >> 31) << 15));
+      else p32[(size_t)j * code->order + v] = (jp * g.ts + tp) | (owner << 16) | (raw & 0x80000000u);
+    }
+  if (pa16) as_bytes(p16);
+  else as_bytes(p32);
+  return out;
+}
+
+
+
 int sm_count(int device) {
   int n = 0;
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 1;
@@ -242,41 +289,9 @@ int prepare_side(lead_code* code, int s) {
   // or, for larger shapes, address | owner rank << 16 | first << 31 (u32).
   {
     const Geometry g = bp_geometry(code, s);
-    if (g.cluster == 1 && (size_t)nl * g.ts < 32768) {
-      std::vector<uint16_t> pa((size_t)nl * g.ts, 0);
-      for (int sl = 0; sl < g.spb; ++sl)
-        for (int v = 0; v < code->order; ++v)
-          for (int j = 0; j < nl; ++j) {
-            const uint32_t raw = hs.partner[(size_t)v * nl + j];
-            const uint32_t ps = raw & 0x7FFFFFFFu;
-            const uint32_t vp = ps / nl, jp = ps % nl;
-            const int t = sl * code->order + v;
-            pa[(size_t)j * g.ts + t] = (uint16_t)((jp * g.ts + sl * code->order + vp) | ((raw >> 31) << 15));
-          }
-      LEAD_TRY(upload(&ds.bp_pa, pa));
-    } else if (cluster_pa16(g, nl)) {
-      // cluster launch, u16 entries: partner word address | owner rank << 13 | first << 15
-      std::vector<uint16_t> pa((size_t)nl * code->order, 0);
-      for (int v = 0; v < code->order; ++v)
-        for (int j = 0; j < nl; ++j) {
-          const uint32_t raw = hs.partner[(size_t)v * nl + j];
-          const uint32_t ps = raw & 0x7FFFFFFFu;
-          const uint32_t vp = ps / nl, jp = ps % nl;
-          const uint32_t owner = vp / g.ts, tp = vp - owner * g.ts;
-          pa[(size_t)j * code->order + v] = (uint16_t)((jp * g.ts + tp) | (owner << 13) | ((raw >> 31) << 15));
-        }
-      LEAD_TRY(upload(&ds.bp_pa, pa));
-    } else if (g.cluster > 1) {
-      std::vector<uint32_t> pa((size_t)nl * code->order, 0);
-      for (int v = 0; v < code->order; ++v)
-        for (int j = 0; j < nl; ++j) {
-          const uint32_t raw = hs.partner[(size_t)v * nl + j];
-          const uint32_t ps = raw & 0x7FFFFFFFu;
-          const uint32_t vp = ps / nl, jp = ps % nl;
-          const uint32_t owner = vp / g.ts, tp = vp - owner * g.ts;
-          pa[(size_t)j * code->order + v] = (jp * g.ts + tp) | (owner << 16) | (raw & 0x80000000u);
-        }
-      uint32_t* d = nullptr;
+    const std::vector<uint8_t> pa = partner_table_bytes(code, s, g);
+    if (!pa.empty()) {
+      uint8_t* d = nullptr;
       LEAD_TRY(upload(&d, pa));
       ds.bp_pa = reinterpret_cast<uint16_t*>(d);
     }

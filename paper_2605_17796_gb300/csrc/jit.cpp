@@ -9,6 +9,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -29,7 +30,7 @@ namespace {
 // Bytes of one stored LLR in a precision mode.
 static size_t msg_bytes(int prec) { return prec == LEAD_PREC_FP32 ? 4 : 2; }
 
-Geometry bp_geometry(const lead_code* code, int side, int prec) {
+Geometry bp_geometry(const lead_code* code, int side, int prec, int spb_req, int cluster_req) {
   const SideParams& P = code->side[side].params;
   Geometry g{};
   // With one shot per CTA (or per cluster) the staged syndrome row lives in the posterior array
@@ -45,7 +46,8 @@ Geometry bp_geometry(const lead_code* code, int side, int prec) {
   auto smem_for = [&](int ts, int spb, size_t mb) {
     const size_t msgs = ((size_t)ts * code->nl * 3 * mb + 15) & ~size_t(15);
     if (aliased(ts, spb, mb)) return msgs + 16;
-    return msgs + sizeof(uint32_t) * ((size_t)spb * P.words_m + (size_t)spb * code->words_n + 2 * (size_t)spb + 2);
+    // staged syndromes, correction bits and three verdict words per shot (one spare word)
+    return msgs + sizeof(uint32_t) * ((size_t)spb * P.words_m + (size_t)spb * code->words_n + 3 * (size_t)spb + 1);
   };
   // The split of shots and vertices over CTAs is fixed by the binary32 footprint, so every
   // precision mode shares one partner table; the 16-bit modes only need less shared memory.
@@ -60,6 +62,14 @@ Geometry bp_geometry(const lead_code* code, int side, int prec) {
     g.spb = 1;
     g.ts = (code->order + g.cluster - 1) / g.cluster;
     smem32 = smem_for(g.ts, 1, 4);
+  }
+  if (spb_req > 0 && g.cluster == 1) {     // another number of shots per CTA (autotuning)
+    g.spb = spb_req;
+    g.ts = g.spb * code->order;
+  }
+  if (cluster_req > 1 && g.cluster > 1) {  // another cluster size (autotuning)
+    g.cluster = cluster_req;
+    g.ts = (code->order + g.cluster - 1) / g.cluster;
   }
   g.smem = smem_for(g.ts, g.spb, msg_bytes(prec));
   g.alias = aliased(g.ts, g.spb, msg_bytes(prec));
@@ -123,9 +133,7 @@ std::string prelude(const lead_code* code, int side, const Geometry& g, int prec
       s << "}";
     }
   }
-  s << "};\n__device__ constexpr unsigned long long kRowMask[" << P.m_l << "] = {";
-  for (int r = 0; r < P.m_l; ++r) s << (r ? "," : "") << P.rowmask[r] << "ull";
-  // the same rows over the two words of the kernel's hard-decision bits: local index j < 32 at
+  // the local rows over the two words of the kernel's hard-decision bits: local index j < 32 at
   // bit nlo - 1 - j of the low word (nlo = min(nl, 32)), j >= 32 at bit nl - 1 - j of the high one
   const int nlo = std::min(code->nl, 32);
   for (int part = 0; part < 2; ++part) {
@@ -292,13 +300,36 @@ int jit_ensure(const lead_code* ccode, int side, int prec) {
   return load_one(code, side, prec);
 }
 
+void release_tuned(TunedKernel& t) {
+  if (t.owned && t.lib) cudaLibraryUnload(static_cast<cudaLibrary_t>(t.lib));
+  cudaFree(t.pa);
+  t = TunedKernel{};
+}
+
 void jit_unload(lead_code* code) {
   for (auto& ds : code->dside)
     for (int prec = 0; prec < kPrecModes; ++prec) {
+      for (auto& t : ds.tuned[prec]) release_tuned(t);
+      ds.tuned[prec].clear();
       if (ds.bp_module[prec]) cudaLibraryUnload(static_cast<cudaLibrary_t>(ds.bp_module[prec]));
       ds.bp_module[prec] = nullptr;
       ds.bp_func[prec] = nullptr;
     }
+}
+
+// The tuned launch shape for prior p: the one whose tuning prior is nearest on a log scale, or
+// null (the default kernel) when none was tuned.
+const TunedKernel* tuned_for(const DeviceSide& ds, int prec, double p) {
+  const TunedKernel* best = nullptr;
+  double dbest = 0.0;
+  for (const TunedKernel& t : ds.tuned[prec]) {
+    const double d = std::fabs(std::log(std::max(p, 1e-12) / t.p));
+    if (!best || d < dbest) {
+      best = &t;
+      dbest = d;
+    }
+  }
+  return best;
 }
 
 int jit_launch_bp(const lead_code* code, int side, int prec, const BPJitArgs& args, int sm_count, void* stream) {
@@ -311,29 +342,37 @@ int jit_launch_bp(const lead_code* code, int side, int prec, const BPJitArgs& ar
   } else if (!ds.bp_func[prec]) {
     return LEAD_ESTATE;
   }
-  const long long groups = (args.shots + hs.bp_spb - 1) / hs.bp_spb;     // shots per CTA or per cluster
-  const long long units = std::max<long long>(1, ((long long)sm_count * ds.bp_per_sm[prec]) / hs.bp_cluster);
-  const long long blocks = std::min<long long>(groups, units) * hs.bp_cluster;
+  const TunedKernel* t = tuned_for(ds, prec, args.p);
+  const int spb = t ? t->spb : hs.bp_spb, cl = t ? t->cluster : hs.bp_cluster;
+  const int per_sm = t ? t->per_sm : ds.bp_per_sm[prec], block = t ? t->block : hs.bp_block;
+  const size_t smem = t ? t->smem : hs.bp_smem[prec];
+  const long long groups = (args.shots + spb - 1) / spb;     // shots per CTA or per cluster
+  const long long units = std::max<long long>(1, ((long long)sm_count * per_sm) / cl);
+  const long long blocks = std::min<long long>(groups, units) * cl;
   BPJitArgs a = args;
+  a.spb = spb;
+  if (t && t->pa) a.pa = t->pa;        // the partner table of the tuned shape
   void* params[] = {&a};
-  if (cudaLaunchKernel(ds.bp_func[prec], dim3((unsigned)blocks), dim3(hs.bp_block), params, hs.bp_smem[prec],
+  if (cudaLaunchKernel(t ? t->func : ds.bp_func[prec], dim3((unsigned)blocks), dim3(block), params, smem,
                        static_cast<cudaStream_t>(stream)) != cudaSuccess)
     return LEAD_ECUDA;
   return LEAD_OK;
 }
 
-// Autotuning of one side's kernel in one precision mode: the resident CTAs per SM, i.e. the
-// register cap per thread, from what shared memory allows down to at most three fewer. Every
-// candidate is compiled, loaded and timed (CUDA events, one warm-up and two timed calls of
-// lead_decode) on `shots` shots sampled at p; the fastest is kept for every later call. The
-// geometry (slots, shots per CTA, cluster) and so every output is the same for all candidates.
+// Autotuning of one side's kernel in one precision mode over its launch shape: the shots per CTA
+// (one-CTA codes: one to four times the default, where the block and shared memory allow) or
+// the cluster size (codes split over a cluster: 2, 3, 4 or 7 CTAs) and, for each, the resident
+// CTAs per SM (the register cap per thread) from what shared memory allows down to two fewer.
+// Every candidate is compiled, loaded and timed (CUDA events, one warm-up and two timed calls of
+// lead_decode) on `shots` shots sampled at p, and the fastest is kept as the shape of later calls
+// whose prior is nearest to p on a log scale (how many iterations shots take, and how unevenly,
+// decides which shape wins). Every candidate runs the same arithmetic on every shot, so the
+// outputs do not depend on the choice.
 int autotune_one(lead_code* code, int side, int prec, double p, int64_t shots, std::string* report) {
   HostSide& hs = code->side[side];
   DeviceSide& ds = code->dside[side];
   int rc = jit_ensure(code, side, prec);            // the default kernel, compiled and loaded
   if (rc != LEAD_OK) return rc;
-  Geometry g = bp_geometry(code, side, prec);
-  const int top = g.minblocks;
   const int wm = hs.params.words_m, wn = code->words_n;
   uint32_t *err = nullptr, *syn = nullptr, *corr = nullptr;
   uint8_t* st = nullptr;
@@ -389,74 +428,104 @@ int autotune_one(lead_code* code, int side, int prec, double p, int64_t shots, s
     *ms *= 0.5f;
     return LEAD_OK;
   };
+  // one launch shape: the kernel, its geometry and its partner table (null: the default one)
   struct Cand {
-    int minblocks, maxreg, per_sm;
-    long spill;
-    float ms;
+    TunedKernel k;
+    int minblocks = -1;
+    long spill = 0;
+    float ms = 0.0f;
     std::vector<char> cubin;
-    void* lib;
-    void* kern;
   };
+  // every candidate is timed as the only tuned shape (the default kernel: none); the list of
+  // shapes tuned before is put back afterwards
+  std::vector<TunedKernel> saved;
+  saved.swap(ds.tuned[prec]);
   std::vector<Cand> cands;
-  // the kernel in use first (compile_one's choice), then every other occupancy
   {
-    Cand c{};
-    c.minblocks = -1;
-    c.maxreg = hs.bp_maxreg[prec];
-    c.per_sm = ds.bp_per_sm[prec];
-    c.cubin = hs.bp_cubin[prec];
-    c.lib = ds.bp_module[prec];
-    c.kern = ds.bp_func[prec];
+    Cand c;                                   // the default kernel
+    c.k.p = p;
+    c.k.lib = ds.bp_module[prec];
+    c.k.func = ds.bp_func[prec];
+    c.k.per_sm = ds.bp_per_sm[prec];
+    c.k.block = hs.bp_block;
+    c.k.spb = hs.bp_spb;
+    c.k.cluster = hs.bp_cluster;
+    c.k.maxreg = hs.bp_maxreg[prec];
+    c.k.smem = hs.bp_smem[prec];
     rc = time_current(&c.ms);
-    if (rc != LEAD_OK) {
-      cleanup();
-      return rc;
-    }
     cands.push_back(std::move(c));
   }
-  for (int m = top; m >= std::max(1, top - 3) && rc == LEAD_OK; --m) {
-    Geometry gm = g;
-    gm.minblocks = m;
-    Cand c{};
-    c.minblocks = m;
-    c.maxreg = std::min(255, (65536 / (g.block * m)) & ~7);
-    if (c.maxreg == hs.bp_maxreg[prec]) continue;     // the kernel in use
-    std::string log;
-    rc = nvrtc_build(prelude(code, side, gm, prec) + kLeadJitSource, c.maxreg, &c.cubin, &log);
+  // launch shapes: (shots per CTA, cluster size)
+  std::vector<std::pair<int, int>> shapes;
+  if (hs.bp_cluster == 1) {
+    for (int f = 1; f <= 4; ++f) shapes.push_back({hs.bp_spb * f, 1});
+  } else {
+    // the default, and the sizes that leave few idle lanes in the last warp of a CTA for the
+    // codes here (a cluster is at most 8 CTAs, the portable limit)
+    shapes.push_back({1, hs.bp_cluster});
+    for (int c : {2, 3, 4, 7})
+      if (c != hs.bp_cluster) shapes.push_back({1, c});
+  }
+  for (const auto& shape : shapes) {
     if (rc != LEAD_OK) break;
-    c.spill = spill_bytes(log);
-    cudaLibrary_t lib = nullptr;
-    cudaKernel_t kern = nullptr;
-    const char* name = hs.bp_cluster > 1 ? "lead_bp_jit_cluster" : "lead_bp_jit";
-    if (cudaLibraryLoadData(&lib, c.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
-        cudaLibraryGetKernel(&kern, lib, name) != cudaSuccess ||
-        cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs.bp_smem[prec]) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, (const void*)kern, hs.bp_block, hs.bp_smem[prec]) !=
-            cudaSuccess ||
-        c.per_sm < 1) {
-      if (lib) cudaLibraryUnload(lib);
-      rc = LEAD_ECUDA;
-      break;
+    const int spb = shape.first;
+    const Geometry g = bp_geometry(code, side, prec, spb, shape.second);
+    if (g.block > 1024 || g.smem > 227u * 1024u) continue;
+    if (g.cluster == 1 && (size_t)code->nl * g.ts >= 32768) continue;
+    if (g.cluster > 1 && (size_t)code->nl * g.ts >= 65536) continue;      // u32 table: 16-bit addresses
+    for (int m = g.minblocks; m >= std::max(1, g.minblocks - 2) && rc == LEAD_OK; --m) {
+      Geometry gm = g;
+      gm.minblocks = m;
+      Cand c;
+      c.minblocks = m;
+      c.k.p = p;
+      c.k.owned = true;
+      c.k.spb = spb;
+      c.k.cluster = g.cluster;
+      c.k.block = g.block;
+      c.k.smem = g.smem;
+      c.k.maxreg = std::min(255, (65536 / (g.block * m)) & ~7);
+      if (spb == hs.bp_spb && g.cluster == hs.bp_cluster && c.k.maxreg == hs.bp_maxreg[prec]) continue;   // default
+      std::string log;
+      rc = nvrtc_build(prelude(code, side, gm, prec) + kLeadJitSource, c.k.maxreg, &c.cubin, &log);
+      if (rc != LEAD_OK) break;
+      c.spill = spill_bytes(log);
+      cudaLibrary_t lib = nullptr;
+      cudaKernel_t kern = nullptr;
+      const char* name = g.cluster > 1 ? "lead_bp_jit_cluster" : "lead_bp_jit";
+      if (cudaLibraryLoadData(&lib, c.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess ||
+          cudaLibraryGetKernel(&kern, lib, name) != cudaSuccess ||
+          cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem) !=
+              cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.k.per_sm, (const void*)kern, g.block, g.smem) !=
+              cudaSuccess ||
+          c.k.per_sm < 1) {
+        if (lib) cudaLibraryUnload(lib);
+        rc = LEAD_ECUDA;
+        break;
+      }
+      c.k.lib = lib;
+      c.k.func = kern;
+      if (spb != hs.bp_spb || g.cluster != hs.bp_cluster) {
+        // this shape's partner table (bytes: u16 entries, or u32 for the larger cluster shapes)
+        const std::vector<uint8_t> pa = partner_table_bytes(code, side, g);
+        if (cudaMalloc(&c.k.pa, pa.size()) != cudaSuccess ||
+            cudaMemcpy(c.k.pa, pa.data(), pa.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+          release_tuned(c.k);
+          rc = LEAD_EOOM;
+          break;
+        }
+      }
+      ds.tuned[prec].assign(1, c.k);          // time it as the only tuned shape
+      rc = time_current(&c.ms);
+      ds.tuned[prec].clear();
+      cands.push_back(std::move(c));
     }
-    c.lib = lib;
-    c.kern = kern;
-    // time it in place of the kernel in use
-    void* old_lib = ds.bp_module[prec];
-    void* old_kern = ds.bp_func[prec];
-    const int old_per_sm = ds.bp_per_sm[prec];
-    ds.bp_module[prec] = lib;
-    ds.bp_func[prec] = kern;
-    ds.bp_per_sm[prec] = c.per_sm;
-    rc = time_current(&c.ms);
-    ds.bp_module[prec] = old_lib;
-    ds.bp_func[prec] = old_kern;
-    ds.bp_per_sm[prec] = old_per_sm;
-    cands.push_back(std::move(c));
   }
   cleanup();
+  ds.tuned[prec].swap(saved);
   if (rc != LEAD_OK) {
-    for (size_t i = 1; i < cands.size(); ++i) cudaLibraryUnload(static_cast<cudaLibrary_t>(cands[i].lib));
+    for (Cand& c : cands) release_tuned(c.k);     // the default entry owns nothing
     return rc;
   }
   size_t best = 0;
@@ -466,20 +535,27 @@ int autotune_one(lead_code* code, int side, int prec, double p, int64_t shots, s
   r << "side " << side << " precision " << prec << ", " << shots << " shots at p = " << p << ":\n";
   for (size_t i = 0; i < cands.size(); ++i) {
     const Cand& c = cands[i];
-    if (c.minblocks < 0) r << "  kernel in use, <= " << c.maxreg << " registers (" << c.per_sm << " resident)";
-    else r << "  " << c.minblocks << " CTA(s) per SM, <= " << c.maxreg << " registers, " << c.spill
-           << " B spilled (" << c.per_sm << " resident)";
-    r << ": " << c.ms << " ms" << (i == best ? "  <- kept" : "") << "\n";
+    r << "  " << (i == 0 ? "default kernel: " : "");
+    if (c.k.cluster > 1) r << "cluster of " << c.k.cluster << " CTAs x " << c.k.block << " threads, ";
+    else r << c.k.spb << " shot(s) per CTA x " << c.k.block << " threads, ";
+    if (c.minblocks > 0) r << c.minblocks << " CTA(s) per SM requested, ";
+    r << "<= " << c.k.maxreg << " registers, ";
+    if (c.minblocks > 0) r << c.spill << " B spilled, ";
+    r << c.k.per_sm << " resident: " << c.ms << " ms" << (i == best ? "  <- kept" : "") << "\n";
   }
   if (report) *report += r.str();
-  // keep the fastest; unload the others (including the kernel in use if it lost)
+  // the fastest becomes the tuned shape for p (replacing one tuned at the same p); the other
+  // candidates are released
   for (size_t i = 0; i < cands.size(); ++i)
-    if (i != best) cudaLibraryUnload(static_cast<cudaLibrary_t>(cands[i].lib));
-  ds.bp_module[prec] = cands[best].lib;
-  ds.bp_func[prec] = cands[best].kern;
-  ds.bp_per_sm[prec] = cands[best].per_sm;
-  hs.bp_cubin[prec] = std::move(cands[best].cubin);
-  hs.bp_maxreg[prec] = cands[best].maxreg;
+    if (i != best) release_tuned(cands[i].k);
+  auto& list = ds.tuned[prec];
+  for (size_t i = 0; i < list.size(); ++i)
+    if (std::fabs(std::log(list[i].p / p)) < 1e-9) {
+      release_tuned(list[i]);
+      list.erase(list.begin() + (long)i);
+      break;
+    }
+  list.push_back(cands[best].k);
   return LEAD_OK;
 }
 

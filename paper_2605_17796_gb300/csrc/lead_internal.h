@@ -30,6 +30,19 @@ struct SideParams {
   uint64_t rowmask[kMaxLocalRows];            // bit j set iff row r touches local index j
 };
 
+// A launch shape of the min-sum kernel kept by lead_code_autotune for calls whose prior is
+// nearest (log scale) to p: its own compiled kernel and, when its shots per CTA or cluster size
+// differ from the default geometry's, its own partner table.
+struct TunedKernel {
+  double p = 0.0;
+  void* lib = nullptr;          // cudaLibrary_t; not owned when it is the default kernel
+  void* func = nullptr;         // cudaKernel_t
+  bool owned = false;
+  int per_sm = 0, block = 0, spb = 1, cluster = 1, maxreg = 0;
+  size_t smem = 0;
+  uint16_t* pa = nullptr;       // owned partner table, or null for the default one
+};
+
 struct DeviceSide {
   uint16_t* views = nullptr;     // order*nl qubit ids
   uint32_t* partner = nullptr;   // order*nl: (other slot) | (this view is the first << 31)
@@ -46,6 +59,7 @@ struct DeviceSide {
   void* bp_module[kPrecModes] = {};   // cudaLibrary_t of the specialised min-sum kernel, per mode
   void* bp_func[kPrecModes] = {};     // its cudaKernel_t
   int bp_per_sm[kPrecModes] = {};     // resident CTAs per SM
+  std::vector<TunedKernel> tuned[kPrecModes];   // launch shapes kept by lead_code_autotune
 };
 
 struct HostSide {
@@ -66,7 +80,7 @@ struct HostSide {
   std::vector<uint32_t> cbase, ckern;
   SideParams params{};
   std::vector<char> bp_cubin[kPrecModes];   // specialised min-sum kernel per mode (NVRTC output)
-  int bp_block = 0, bp_spb = 0, bp_cluster = 1;
+  int bp_block = 0, bp_spb = 0, bp_cluster = 1;   // the default geometry (binary32 footprint)
   size_t bp_smem[kPrecModes] = {};
   int bp_maxreg[kPrecModes] = {};          // register cap per thread it was compiled with
 };
@@ -105,7 +119,17 @@ struct Geometry {               // launch geometry of the min-sum kernel for one
   bool alias;                   // one shot per CTA: syndromes and correction bits share the
                                 // message arrays (see bp_geometry)
 };
-Geometry bp_geometry(const lead_code* code, int side, int prec = LEAD_PREC_FP32);
+// spb > 0 asks for that many shots per CTA instead of the default (one-CTA shots only);
+// cluster > 1 for that cluster size (shots split over a cluster only).
+Geometry bp_geometry(const lead_code* code, int side, int prec = LEAD_PREC_FP32, int spb = 0, int cluster = 0);
+// The u16 partner table of a one-CTA geometry: entry [j][t] = shared-memory word of the partner
+// slot of (j, t) | first view << 15, t = shot sl * order + vertex v.
+std::vector<uint16_t> single_cta_partner_table(const lead_code* code, int side, const Geometry& g);
+// The partner table of any geometry as the bytes the kernel reads: the one-CTA table above, or
+// for a cluster (indexed [j][v], v the global vertex) partner word address inside its owner CTA
+// | owner rank << 13 | first << 15 as u16 when cluster_pa16, else address | rank << 16 |
+// first << 31 as u32.
+std::vector<uint8_t> partner_table_bytes(const lead_code* code, int side, const Geometry& g);
 // Cluster launches whose slot addresses fit 13 bits and owner ranks 2 bits use a u16 partner
 // table (address | owner << 13 | first << 15): half the bytes of the u32 form, so it stays in L1.
 inline bool cluster_pa16(const Geometry& g, int nl) { return g.cluster > 1 && g.cluster <= 4 && nl * g.ts < 8192; }

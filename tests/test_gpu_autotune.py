@@ -1,6 +1,7 @@
 """lead_code_autotune: the min-sum kernel (Algorithm 1, Phase 3) kept after timing several
-register caps decodes every shot bit-identically to the kernel it replaced, in each precision
-mode, and the report names one kept candidate per call."""
+launch shapes (shots per CTA or cluster size, register cap) decodes every shot bit-identically
+to the default kernel, in each precision mode, at the tuned prior and at another one it
+serves, and the report names one kept candidate per call."""
 import numpy as np
 import pytest
 
@@ -44,11 +45,13 @@ def test_tuned_kernel_is_bit_identical(L, name, side, p, shots):
     for precision in (0, 1, 2):
         code = L.Code.from_instance(inst).prepare(0)
         dev = torch.from_numpy(philox.pack_bits(syn, code.info.words_m[side]).view(np.int32)).cuda()
-        before = _decode(L, code, side, dev, shots, p, precision)
+        # decodes at p and at p / 2 (which the shape tuned at p also serves: the nearest tuned p)
+        before = [_decode(L, code, side, dev, shots, q, precision) for q in (p, p / 2)]
         report = code.autotune(side, precision, p, shots=min(4096, 64 * shots))
         print(f"{name} side {side} precision {precision}:\n{report}")
         assert report.count("<- kept") == 1
-        after = _decode(L, code, side, dev, shots, p, precision)
-        for a, b in zip(before, after):
-            assert a.dtype == b.dtype and (a == b).all()
+        after = [_decode(L, code, side, dev, shots, q, precision) for q in (p, p / 2)]
+        for bq, aq in zip(before, after):
+            for a, b in zip(bq, aq):
+                assert a.dtype == b.dtype and (a == b).all()
         assert code.device_errors() == 0

@@ -1,5 +1,8 @@
-"""Multi-code batch in one CUDA-graph launch: every entry's corrections, statuses and failure
-flags equal those of the same entry decoded on its own, eagerly; replays are repeatable."""
+"""Multi-code batch in one CUDA-graph launch (kernels and plan autotuned): every entry's
+corrections, statuses and failure flags equal those of the same entry decoded on its own,
+eagerly, and sampled rows of every code equal the oracle's decode of the same shots; replays
+are repeatable."""
+import numpy as np
 import pytest
 
 import workloads
@@ -36,3 +39,16 @@ def test_graph_batch_equals_separate_runs():
         for k in ("corr", "status", "iters", "fail"):
             for s in (0, 1):
                 assert torch.equal(got[i][k][s], solo.buf[0][k][s]), (i, k, s)
+    # sampled rows of every code against the oracle (depolarizing p = 0.04: each side decoded
+    # with prior 2p/3 from the shot's X or Z part)
+    from oracle import lead as olead, philox, tanner
+    for i, (e, name) in enumerate(zip(entries, ("SL(2,3)", "PSL(2,7)", "PSL(2,11)"))):
+        oc = tanner.from_instance(workloads.standard(name, 0))
+        rows = np.array([0, 5, 77] if name != "PSL(2,11)" else [0, 41])
+        x, z = philox.sample_errors(philox.NOISE_DEPOL, e.p, e.seed, rows, oc.n)
+        for s, err in ((0, x), (1, z)):
+            wc, wst, wit, _ = olead.decode(oc, s, philox.syndromes(oc.sides[s].H, err), 2 * e.p / 3)
+            words = got[i]["corr"][s][rows].cpu().numpy().view(np.uint32)
+            assert (philox.unpack_bits(words, oc.n) == wc).all(), (name, s)
+            assert (got[i]["status"][s][rows].cpu().numpy() == wst).all(), (name, s)
+            assert (got[i]["iters"][s][rows].cpu().numpy() == wit).all(), (name, s)

@@ -6,6 +6,8 @@ every entry point that launches an instrumented kernel, it must:
 * raise no LEAD_ECHECK and leave every code's record at zero;
 * return results identical, byte for byte, to the release build's on the same inputs. The
   release build's results are themselves compared with the oracle in the other GPU tests.
+A decode captured into a CUDA graph and replayed must give the eager call's results, and the
+eager call after it (which reads the record the captured call left) must succeed.
 Each library runs in a child process (the binding loads one library per process); this file is
 also the child's script.
 """
@@ -52,6 +54,22 @@ def _child(out_path):
             c, s, i, post = out()
             code.decode(o, syn, shots, c, s, i, post, ws(code.workspace_bytes(o, shots)))
             res[key + "/decode"] = [c, s, i, post]
+            if name == "PSL(2,7)":
+                # the decode captured into a CUDA graph: a captured call cannot wait for its stream,
+                # so the checked build leaves the record for the next eager call, which reads it
+                cg, sg, ig, pg = out()
+                wsg = ws(code.workspace_bytes(o, shots))
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+                    code.decode(o, syn, shots, cg, sg, ig, pg, wsg)
+                for _ in range(2):
+                    graph.replay()
+                torch.cuda.synchronize()
+                for x, y in zip((cg, sg, ig, pg), (c, s, i, post)):
+                    assert torch.equal(x, y), key
+                res[key + "/graph"] = [cg, sg, ig, pg]
+                code.decode(o, syn, shots, *out(), wsg)       # eager: reads and clears the record
+                del graph
             cb, sb, ib, pb = out()
             code.decode(lead.opts(side=side, p=p, use_lead=False), syn, shots, cb, sb, ib, pb,
                         ws(code.workspace_bytes(o, shots)))
