@@ -164,7 +164,8 @@ int lead_code_compile(lead_code* code, char* log, size_t log_bytes);
  * kernel (Algorithm 1, Phase 3) in one precision mode. The paper has no counterpart: these are
  * properties of this kernel. Candidates: for codes whose shot fits one CTA, one to four times
  * the default shots per CTA; for codes whose shot is split over a thread-block cluster, clusters
- * of 2, 3, 4 and 7 CTAs (where the block stays <= 1024 threads and shared memory fits); for
+ * of 2, 3, 4 and 7 CTAs and one CTA per shot (where the block stays <= 1024 threads and shared
+ * memory fits: in the 16-bit modes, for the codes here); for
  * each, the resident CTAs per SM from what shared memory allows down to two fewer (the register
  * cap per thread trades against them). Each candidate is compiled, loaded and timed with CUDA
  * events (one warm-up and two timed lead_decode calls, Phases 1-3, exact

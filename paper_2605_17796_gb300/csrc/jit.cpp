@@ -67,8 +67,9 @@ Geometry bp_geometry(const lead_code* code, int side, int prec, int spb_req, int
     g.spb = spb_req;
     g.ts = g.spb * code->order;
   }
-  if (cluster_req > 1 && g.cluster > 1) {  // another cluster size (autotuning)
+  if (cluster_req >= 1 && g.cluster > 1) {  // another cluster size, or one CTA per shot (autotuning)
     g.cluster = cluster_req;
+    g.spb = 1;
     g.ts = (code->order + g.cluster - 1) / g.cluster;
   }
   g.smem = smem_for(g.ts, g.spb, msg_bytes(prec));
@@ -361,7 +362,8 @@ int jit_launch_bp(const lead_code* code, int side, int prec, const BPJitArgs& ar
 
 // Autotuning of one side's kernel in one precision mode over its launch shape: the shots per CTA
 // (one-CTA codes: one to four times the default, where the block and shared memory allow) or
-// the cluster size (codes split over a cluster: 2, 3, 4 or 7 CTAs) and, for each, the resident
+// the cluster size (codes split over a cluster: 2, 3, 4 or 7 CTAs, or one CTA per shot where a
+// 16-bit mode's state fits) and, for each, the resident
 // CTAs per SM (the register cap per thread) from what shared memory allows down to two fewer.
 // Every candidate is compiled, loaded and timed (CUDA events, one warm-up and two timed calls of
 // lead_decode) on `shots` shots sampled at p, and the fastest is kept as the shape of later calls
@@ -463,7 +465,7 @@ int autotune_one(lead_code* code, int side, int prec, double p, int64_t shots, s
     // the default, and the sizes that leave few idle lanes in the last warp of a CTA for the
     // codes here (a cluster is at most 8 CTAs, the portable limit)
     shapes.push_back({1, hs.bp_cluster});
-    for (int c : {2, 3, 4, 7})
+    for (int c : {1, 2, 3, 4, 7})       // 1: the whole shot in one CTA, where its state fits
       if (c != hs.bp_cluster) shapes.push_back({1, c});
   }
   for (const auto& shape : shapes) {

@@ -120,7 +120,7 @@ struct Geometry {               // launch geometry of the min-sum kernel for one
                                 // message arrays (see bp_geometry)
 };
 // spb > 0 asks for that many shots per CTA instead of the default (one-CTA shots only);
-// cluster > 1 for that cluster size (shots split over a cluster only).
+// cluster >= 1 for that cluster size (shots split over a cluster only; 1 = one CTA per shot).
 Geometry bp_geometry(const lead_code* code, int side, int prec = LEAD_PREC_FP32, int spb = 0, int cluster = 0);
 // The u16 partner table of a one-CTA geometry: entry [j][t] = shared-memory word of the partner
 // slot of (j, t) | first view << 15, t = shot sl * order + vertex v.

@@ -11,9 +11,9 @@ of its first timed step (replicas.shot_offset(0, 0, 1, p index, 10, 10^6)).
   posterior output): sampled rows (the first 64, 64 spread over the call, the last 8) equal the
   oracle's at p = 0.03, 0.05 and 0.08;
 * the binary32 decision track against the oracle's FP64 track (prior_f64 and min-sum in
-  binary64, same rules), on the 1 000 shots of p = 0.01, 0.03 and 0.05: the shots whose failure
-  verdict differs, and those converged on both tracks with different corrections, are counted
-  and stay under stated bounds.
+  binary64, same rules), on 3 400 benchmark shots at each of p = 0.01, 0.03 and 0.05: the shots
+  whose failure verdict differs, and those converged on both tracks with different corrections,
+  are counted and stay under stated bounds.
 
 The oracle runs in a process pool (spawn) while the GPU decodes.
 """
@@ -37,6 +37,7 @@ JOB = 50
 # binary32 against the FP64 track: the p values compared, and the fractions of shots allowed a
 # different failure verdict, and a different correction among shots converged on both tracks
 F64_P = (0.01, 0.03, 0.05)
+F64_SHOTS_PER_P = 3400        # 10 200 shots over the three p values
 VERDICT_BOUND = 0.02
 CONVERGED_BOUND = 0.01
 
@@ -131,24 +132,25 @@ def test_headline_full_call_sampled_rows(L, code, pool, p):
 
 def test_binary32_track_against_fp64_track(L, code, pool):
     """How often binary32 rounding changes the outcome: the GPU (equal to the oracle's binary32
-    track, above) against the oracle's FP64 track on the same 1 000 shots per p. Min-sum that
+    track, above) against the oracle's FP64 track on 3 400 benchmark shots per p. Min-sum that
     does not converge wanders, and its last decision depends on every rounding, so two counts are
     held: shots whose failure verdict (Sec. IV-A) differs, and shots that converged on both tracks
     with different corrections."""
     n = code.info.n
     for p in F64_P:
         pi = P_SWEEP.index(p)
-        idx = _offset(pi) + np.arange(SHOTS_PER_P)
+        m = F64_SHOTS_PER_P
+        idx = _offset(pi) + np.arange(m)
         futs = [pool.submit(ow.decode_shots, "PSL(2,7)", 0, p, 0, idx[i:i + JOB], True, "f64")
-                for i in range(0, SHOTS_PER_P, JOB)]
-        corr, st, it, _, fail = _gpu_decode(L, code, p, SHOTS_PER_P, _offset(pi), with_post=False)
+                for i in range(0, m, JOB)]
+        corr, st, it, _, fail = _gpu_decode(L, code, p, m, _offset(pi), with_post=False)
         want = _gather(futs)
         st = st.cpu().numpy()
         both = (st == L.ST_CONVERGED) & (want["status"] == L.ST_CONVERGED)
-        diff = (_bits(corr, torch.arange(SHOTS_PER_P, device="cuda"), n) != want["corr"]).any(axis=1)
+        diff = (_bits(corr, torch.arange(m, device="cuda"), n) != want["corr"]).any(axis=1)
         verdict = int(((fail.cpu().numpy() != 0) != (want["fail"] != 0)).sum())
         conv_diff = int((diff & both).sum())
-        print(f"p={p}: failure verdicts differing from the FP64 track {verdict}/{SHOTS_PER_P}; shots "
+        print(f"p={p}: failure verdicts differing from the FP64 track {verdict}/{m}; shots "
               f"converged on both tracks {int(both.sum())}, of them with different corrections {conv_diff}")
-        assert verdict <= VERDICT_BOUND * SHOTS_PER_P
-        assert conv_diff <= CONVERGED_BOUND * SHOTS_PER_P
+        assert verdict <= VERDICT_BOUND * m
+        assert conv_diff <= CONVERGED_BOUND * m
