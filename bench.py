@@ -183,8 +183,28 @@ def _serving(lead, rates, n: int, code_psl7, unloaded_n: int = 2000):
                                    "p99_us": float(np.percentile(((res["done_ns"] - res["arrival_ns"]) / 1e3)[res["code"] == i], 99))}
                             for i, name in enumerate(("PSL(2,7)", "PSL(2,11)"))}
     srv.close()
+    # the same traffic at the top rate in bfloat16 storage, the PSL(2,11) kernels autotuned at
+    # the serving prior first (fresh code objects: the binary32 ones keep their kernels)
+    codes16 = [lead.Code.from_instance(workloads.standard(nm, 0)).prepare(code_psl7.info.prepared_device)
+               for nm in ("PSL(2,7)", "PSL(2,11)")]
+    for side in (0, 1):
+        codes16[1].autotune(side, lead.PREC_BF16, 2 * p / 3, 2048)
+    srv = lead.Server(codes16, [2 * p / 3] * 2, max_batch=256, streams=6, budget_bytes=2 << 30,
+                      precision=lead.PREC_BF16)
+    sv.run_trace(srv, warm_rows, warm_arr, warm_code)
+    bf16_runs = []
+    for k, rate in enumerate(rates):
+        if rate < max(rates):
+            continue
+        rng = np.random.default_rng(k)
+        arrival, code_of = sv.poisson_trace(rate, n, [0.7, 0.3], rng)
+        rows = [sv.request_rows(c, p, int((code_of == i).sum()), seed=100 + 10 * k + i) for i, c in enumerate(codes16)]
+        res, _ = sv.run_trace(srv, rows, arrival, code_of)
+        bf16_runs.append(sv.latency_stats(res, rate))
+    srv.close()
     return {"runs": runs, "unloaded": unloaded, "mix": "70% PSL(2,7) / 30% PSL(2,11)",
-            "noise": "depolarizing p=0.03, both sides", "max_batch": 256, "streams": 6}
+            "noise": "depolarizing p=0.03, both sides", "max_batch": 256, "streams": 6,
+            "bf16_tuned_top_rate": bf16_runs}
 
 
 def _prior_local(lead, code, tc_peak_tflops: float, shots: int = 1 << 15, p: float = 0.02):

@@ -468,7 +468,10 @@ int lead_check(const lead_code* code, int32_t side, const uint32_t* err, const u
  * shots whenever a stream slot is free, and keeps up to `streams` batches in flight (their
  * kernels overlap on the device). Each slot owns device buffers for max_batch shots; the number
  * of slots is min(streams, budget_bytes / slot size) (admission by memory; LEAD_EOOM if not even
- * one fits). lead_server_create builds, once, the Phase 1-2 tables of every code and side (the
+ * one fits). Each batch runs the min-sum kernel in cfg->precision (as lead_decode with that
+ * storage format; a 16-bit mode's kernel is compiled and loaded at creation), with the launch
+ * shape lead_code_autotune kept nearest to the code's p_side, if any.
+ * lead_server_create builds, once, the Phase 1-2 tables of every code and side (the
  * local posterior table for the code's p and its class tables, as lead_decode would); every
  * batch then runs lead_decode's min-sum kernel on the sides in sides_mask with those tables and
  * copies corrections and statuses back; completion is detected with cudaEventQuery. A result
@@ -486,6 +489,7 @@ typedef struct {
   size_t budget_bytes;       /* device memory the slots may use                                  */
   int32_t max_iter;
   float alpha;
+  int32_t precision;         /* LEAD_PREC_*: storage format of the min-sum kernel (0 = binary32) */
 } lead_server_config;
 
 typedef struct {

@@ -70,7 +70,7 @@ struct Slot {
 struct lead_server {
   std::vector<lead_code*> codes;
   std::vector<double> p_side;
-  int32_t sides_mask = 3, max_batch = 0, max_iter = 32;
+  int32_t sides_mask = 3, max_batch = 0, max_iter = 32, precision = LEAD_PREC_FP32;
   float alpha = 1.0f;
   int32_t wm[2] = {0, 0}, wn = 0;    // maxima over the codes
   std::vector<void*> tables;          // per code, per side: local posterior table + class tables
@@ -112,7 +112,7 @@ int launch_batch(lead_server* s, Slot& sl) {
     o.side = side;
     o.use_lead = 1;
     o.max_iter = s->max_iter;
-    o.precision = LEAD_PREC_FP32;
+    o.precision = s->precision;
     o.alpha = s->alpha;
     o.p = s->p_side[sl.code];
     char* tab = static_cast<char*>(s->tables[2 * (size_t)sl.code + side]);
@@ -248,6 +248,8 @@ int build_tables(lead_server* s) {
       if (rc == LEAD_OK)
         rc = lead::launch_classify(code, side, s->alpha, LEAD_PREC_FP32, static_cast<float*>(t),
                                    static_cast<char*>(t) + lead::table_bytes_of(code, side), st);
+      // the storage mode's kernel, compiled and loaded now rather than in the first batch
+      if (rc == LEAD_OK) rc = lead::jit_ensure(code, side, s->precision);
     }
   }
   if (cudaStreamSynchronize(st) != cudaSuccess && rc == LEAD_OK) rc = LEAD_ECUDA;
@@ -260,7 +262,8 @@ int build_tables(lead_server* s) {
 extern "C" {
 
 int lead_server_create(const lead_server_config* cfg, lead_server** out) {
-  if (!cfg || !out || cfg->ncodes < 1 || !cfg->codes || !cfg->p_side || cfg->max_batch < 1 || cfg->streams < 1)
+  if (!cfg || !out || cfg->ncodes < 1 || !cfg->codes || !cfg->p_side || cfg->max_batch < 1 || cfg->streams < 1 ||
+      cfg->precision < 0 || cfg->precision >= lead::kPrecModes)
     return LEAD_EINVAL;
   *out = nullptr;
   lead_server* s = new (std::nothrow) lead_server();
@@ -269,6 +272,7 @@ int lead_server_create(const lead_server_config* cfg, lead_server** out) {
   s->max_batch = cfg->max_batch;
   s->max_iter = cfg->max_iter;
   s->alpha = cfg->alpha;
+  s->precision = cfg->precision;
   s->device = -1;
   for (int c = 0; c < cfg->ncodes; ++c) {
     lead_code* code = cfg->codes[c];

@@ -52,7 +52,7 @@ class LeadServerConfig(ctypes.Structure):
     _fields_ = [("ncodes", ctypes.c_int32), ("codes", ctypes.POINTER(ctypes.c_void_p)),
                 ("p_side", ctypes.POINTER(ctypes.c_double)), ("sides_mask", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32), ("budget_bytes", ctypes.c_size_t),
-                ("max_iter", ctypes.c_int32), ("alpha", ctypes.c_float)]
+                ("max_iter", ctypes.c_int32), ("alpha", ctypes.c_float), ("precision", ctypes.c_int32)]
 
 
 class LeadServerResult(ctypes.Structure):
@@ -389,13 +389,13 @@ class Server:
     times, poll results. Codes must be prepared on the same device."""
 
     def __init__(self, codes, p_side, sides_mask: int = 3, max_batch: int = 256, streams: int = 4,
-                 budget_bytes: int = 1 << 30, max_iter: int = 32, alpha: float = 1.0):
+                 budget_bytes: int = 1 << 30, max_iter: int = 32, alpha: float = 1.0, precision: int = 0):
         self.codes = list(codes)
         self._handles = (ctypes.c_void_p * len(self.codes))(*[c._h.value for c in self.codes])
         self._p = (ctypes.c_double * len(self.codes))(*p_side)
         cfg = LeadServerConfig(ncodes=len(self.codes), codes=self._handles, p_side=self._p, sides_mask=sides_mask,
                                max_batch=max_batch, streams=streams, budget_bytes=budget_bytes, max_iter=max_iter,
-                               alpha=alpha)
+                               alpha=alpha, precision=precision)
         out = ctypes.c_void_p()
         _check("lead_server_create", LIB.lead_server_create(ctypes.byref(cfg), ctypes.byref(out)))
         self._h = out

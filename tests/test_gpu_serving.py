@@ -118,3 +118,46 @@ def test_memory_admission(setup):
                                  np.zeros(20, dtype=np.int32))
     _check(res, cor, codes, ref, lambda rid: (0, rid))
     srv.close()
+
+
+def test_bfloat16_server_matches_bfloat16_batch_decode(setup):
+    """A server in bfloat16 storage (its codes autotuned at the serving prior first, so the
+    batches run the tuned launch shapes) returns for every request the bfloat16 batch decode of
+    the same shot."""
+    lead, serving, _, rows, _, p = setup
+    codes = [lead.Code.from_instance(workloads.standard(n, 0)).prepare(0) for n in NAMES]
+    for c in codes[1:]:
+        for side in (0, 1):
+            c.autotune(side, lead.PREC_BF16, 2 * p / 3, 512)
+    ref = []
+    for c, r in zip(codes, rows):
+        info = c.info
+        n = r.shape[0]
+        out = {}
+        for side in (0, 1):
+            off = 0 if side == 0 else info.words_m[0]
+            syn = torch.from_numpy(np.ascontiguousarray(r[:, off:off + info.words_m[side]]).view(np.int32)).cuda()
+            o = lead.opts(side=side, p=2 * p / 3, precision=lead.PREC_BF16)
+            ws = torch.zeros(c.workspace_bytes(o) // 4 + 64, dtype=torch.int32, device="cuda")
+            corr = torch.zeros((n, info.words_n), dtype=torch.int32, device="cuda")
+            st = torch.zeros(n, dtype=torch.uint8, device="cuda")
+            c.decode(o, syn, n, corr, st, workspace=ws)
+            out[side] = (corr.cpu().numpy().view(np.uint32), st.cpu().numpy())
+        ref.append(out)
+    torch.cuda.synchronize()
+    srv = lead.Server(codes, [2 * p / 3] * 3, max_batch=32, streams=3, budget_bytes=256 << 20,
+                      precision=lead.PREC_BF16)
+    rng = np.random.default_rng(3)
+    n = sum(r.shape[0] for r in rows)
+    arrival, _ = serving.poisson_trace(2e5, n, [1, 1, 1], rng)
+    code_of = np.concatenate([[c] * r.shape[0] for c, r in enumerate(rows)]).astype(np.int32)[rng.permutation(n)]
+    res, cor = serving.run_trace(srv, rows, arrival, code_of)
+    idx = np.zeros(n, dtype=np.int64)
+    for c in range(len(codes)):
+        sel = np.nonzero(code_of == c)[0]
+        idx[sel] = np.arange(sel.size)
+    _check(res, cor, codes, ref, lambda rid: (int(code_of[rid]), int(idx[rid])))
+    assert srv.pending() == 0
+    srv.close()
+    with pytest.raises(lead.LeadError):
+        lead.Server(codes, [2 * p / 3] * 3, precision=3)
