@@ -307,6 +307,8 @@ int lead_local_estimate(const lead_code* code, const lead_decode_opts* opts, con
  *  applied after rounding), each U_v (summed in binary32, rounded once) and post_i rounded to
  *  nearest even in that format; the hard decision reads the stored posterior. The first call
  *  in a 16-bit mode compiles (unless lead_code_compile ran) and loads that mode's kernel.
+ *  Launch shape: the one lead_code_autotune kept for this side and mode at the tuned prior
+ *  nearest to opts->p (log scale), else the default; the outputs do not depend on it.
  * shots == 0 is a no-op (pointers may then be NULL).
  * Errors: LEAD_EINVAL (including max_iter > 64, alpha outside (0,1] or an unknown precision;
  *        codes whose vertex count times the shared memory of one shot exceed one CTA),
