@@ -473,6 +473,7 @@ int lead_check(const lead_code* code, int32_t side, const uint32_t* err, const u
  * one fits). Each batch runs the min-sum kernel in cfg->precision (as lead_decode with that
  * storage format; a 16-bit mode's kernel is compiled and loaded at creation), with the launch
  * shape lead_code_autotune kept nearest to the code's p_side, if any.
+ * The two sides of a batch decode concurrently (two streams per slot).
  * lead_server_create builds, once, the Phase 1-2 tables of every code and side (the
  * local posterior table for the code's p and its class tables, as lead_decode would); every
  * batch then runs lead_decode's min-sum kernel on the sides in sides_mask with those tables and

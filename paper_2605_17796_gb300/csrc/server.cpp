@@ -53,7 +53,9 @@ struct Request {
 
 struct Slot {
   cudaStream_t stream = nullptr;
+  cudaStream_t stream1 = nullptr;   // side 1's decode, concurrent with side 0's
   cudaEvent_t done = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   uint32_t* d_syn = nullptr;     // max_batch x (wm0 + wm1)
   uint32_t* d_corr = nullptr;    // 2 x max_batch x words_n
   uint8_t* d_status = nullptr;   // 2 x max_batch
@@ -106,8 +108,15 @@ int launch_batch(lead_server* s, Slot& sl) {
                           sizeof(uint32_t) * w, n, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
       return LEAD_ECUDA;
   }
+  // the two sides decode independently: side 1 on the slot's second stream, joined before the
+  // copies back
+  const bool both = (s->sides_mask & 3) == 3;
+  if (both && (cudaEventRecord(sl.fork, sl.stream) != cudaSuccess ||
+               cudaStreamWaitEvent(sl.stream1, sl.fork, 0) != cudaSuccess))
+    return LEAD_ECUDA;
   for (int side = 0; side < 2; ++side) {
     if (!((s->sides_mask >> side) & 1)) continue;
+    cudaStream_t st = (both && side == 1) ? sl.stream1 : sl.stream;
     lead_decode_opts o{};
     o.side = side;
     o.use_lead = 1;
@@ -118,10 +127,13 @@ int launch_batch(lead_server* s, Slot& sl) {
     char* tab = static_cast<char*>(s->tables[2 * (size_t)sl.code + side]);
     int rc = lead::launch_bp(code, &o, d_side[side], n, sl.d_corr + (size_t)side * s->max_batch * s->wn,
                              sl.d_status + (size_t)side * s->max_batch, nullptr, nullptr,
-                             reinterpret_cast<const float*>(tab), sl.stream, nullptr,
+                             reinterpret_cast<const float*>(tab), st, nullptr,
                              tab + lead::table_bytes_of(code, side));
     if (rc != LEAD_OK) return rc;
   }
+  if (both && (cudaEventRecord(sl.join, sl.stream1) != cudaSuccess ||
+               cudaStreamWaitEvent(sl.stream, sl.join, 0) != cudaSuccess))
+    return LEAD_ECUDA;
   for (int side = 0; side < 2; ++side) {
     // device rows have the code's own pitch (words_n); host rows the server's widest pitch
     if (cudaMemcpy2DAsync(sl.h_corr + (size_t)side * s->max_batch * s->wn, sizeof(uint32_t) * s->wn,
@@ -215,8 +227,12 @@ void run(lead_server* s) {
 void free_slots(lead_server* s) {
   for (Slot& sl : s->slots) {
     if (sl.stream) cudaStreamSynchronize(sl.stream);
+    if (sl.stream1) cudaStreamSynchronize(sl.stream1);
     if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.fork) cudaEventDestroy(sl.fork);
+    if (sl.join) cudaEventDestroy(sl.join);
     if (sl.stream) cudaStreamDestroy(sl.stream);
+    if (sl.stream1) cudaStreamDestroy(sl.stream1);
     cudaFree(sl.d_syn);
     cudaFree(sl.d_corr);
     cudaFree(sl.d_status);
@@ -305,7 +321,10 @@ int lead_server_create(const lead_server_config* cfg, lead_server** out) {
     const size_t wsyn = (size_t)s->max_batch * (s->wm[0] + s->wm[1]);
     const size_t wcor = 2 * (size_t)s->max_batch * s->wn;
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sl.stream1, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.join, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&sl.d_syn, sizeof(uint32_t) * wsyn) != cudaSuccess ||
         cudaMalloc(&sl.d_corr, sizeof(uint32_t) * wcor) != cudaSuccess ||
         cudaMalloc(&sl.d_status, 2 * (size_t)s->max_batch) != cudaSuccess ||
