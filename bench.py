@@ -559,21 +559,32 @@ def main():
             pipe.code.sample(lead.NOISE_X, p, e2e_shots, 7, 0, err_x=pipe.err[0], syn_z=pipe.syn[0])
             hsyn[p] = pipe.syn[0][:e2e_shots].cpu().pin_memory()
             herr[p] = pipe.err[0][:e2e_shots].cpu().pin_memory()
-        hcorr = torch.empty((e2e_shots, info.words_n), dtype=torch.int32).pin_memory()
-        hfail = torch.empty(e2e_shots, dtype=torch.uint8).pin_memory()
-        hstat = torch.empty(e2e_shots, dtype=torch.uint8).pin_memory()
+        # two streams take alternate p values with their own rows of the pipeline's buffers, own
+        # workspace and own pinned result buffers, so one p's copies overlap the other's decode
+        streams = [stream, torch.cuda.Stream()]
+        wss = [pipe.workspace, torch.zeros_like(pipe.workspace)]
+        hout = [{"corr": torch.empty((e2e_shots, info.words_n), dtype=torch.int32).pin_memory(),
+                 "fail": torch.empty(e2e_shots, dtype=torch.uint8).pin_memory(),
+                 "stat": torch.empty(e2e_shots, dtype=torch.uint8).pin_memory()} for _ in range(2)]
 
         def e2e_step():
-            for p in P_SWEEP:
-                pipe.syn[0][:e2e_shots].copy_(hsyn[p], non_blocking=True)
-                pipe.err[0][:e2e_shots].copy_(herr[p], non_blocking=True)
-                o = lead.opts(side=0, p=p)
-                orig_decode(o, pipe.syn[0], e2e_shots, pipe.corr[0], pipe.status[0], pipe.iters[0],
-                            workspace=pipe.workspace)
-                code.check(0, pipe.err[0], pipe.corr[0], e2e_shots, pipe.fail[0])
-                hcorr.copy_(pipe.corr[0][:e2e_shots], non_blocking=True)
-                hfail.copy_(pipe.fail[0][:e2e_shots], non_blocking=True)
-                hstat.copy_(pipe.status[0][:e2e_shots], non_blocking=True)
+            streams[1].wait_stream(stream)       # after whatever the step follows (its start event)
+            for k, p in enumerate(P_SWEEP):
+                b = k % 2
+                rows = slice(b * e2e_shots, (b + 1) * e2e_shots)
+                st = streams[b]
+                with torch.cuda.stream(st):
+                    syn, err = pipe.syn[0][rows], pipe.err[0][rows]
+                    corr, sta, its, fail = pipe.corr[0][rows], pipe.status[0][rows], pipe.iters[0][rows], pipe.fail[0][rows]
+                    syn.copy_(hsyn[p], non_blocking=True)
+                    err.copy_(herr[p], non_blocking=True)
+                    o = lead.opts(side=0, p=p)
+                    orig_decode(o, syn, e2e_shots, corr, sta, its, workspace=wss[b], stream=st)
+                    code.check(0, err, corr, e2e_shots, fail, stream=st)
+                    hout[b]["corr"].copy_(corr, non_blocking=True)
+                    hout[b]["fail"].copy_(fail, non_blocking=True)
+                    hout[b]["stat"].copy_(sta, non_blocking=True)
+            stream.wait_stream(streams[1])
         for _ in range(2):
             e2e_step()
         torch.cuda.synchronize()
