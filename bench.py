@@ -414,8 +414,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=1 << 20)
     ap.add_argument("--oracle-shots-per-p", type=int, default=3,
                     help="reference arm: oracle shots per p per process and step")
-    ap.add_argument("--baseline-shots-per-p", type=int, default=100,
-                    help="cpu_baseline leg: oracle shots per p per process (about 30 s of decoding)")
+    ap.add_argument("--baseline-shots-per-p", type=int, default=120,
+                    help="cpu_baseline leg: oracle shots per p per process (a little over 30 s of decoding)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-child", nargs="+")
     ap.add_argument("--serving-rates", type=float, nargs="+", default=[1e5, 3e5, 1e6])
